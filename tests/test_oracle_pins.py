@@ -1,0 +1,426 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test names the passage it follows.  None of them re-types the oracle's own
+formulas: they check closed forms, exact discrete solutions, printed numbers and
+printed derivatives, brute force and finite differences.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import assemble as A
+from oracle import element as El
+from oracle import grid as G
+from oracle import solve as S
+from paper_1508_04596_gb300 import synth
+
+
+def make(nx, ny, nz, h, Gr=1e3, Pr=0.71, bc=None, se=None, force=None, **mat):
+    g = G.Grid(nx, ny, nz, h)
+    bc = G.BCs() if bc is None else bc
+    m, v = G.dirichlet(g, bc)
+    kw = dict(synth.MATERIAL)
+    kw.update(mat)
+    prm = El.Params(h, Gr, Pr, **kw)
+    return g, bc, A.Problem(g, prm, m, v, flux=G.neumann_rhs(g, bc), se=se, force=force)
+
+
+# ---------------------------------------------------------------- counts
+def test_dof_counts_printed():
+    """Sec. 6.2-6.4: the printed DOF and element counts (tests/golden/paper_dof_counts.txt)
+    follow from 5 unknowns on every node of the structured grid."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_dof_counts.txt")
+    rows = [l.split()[:5] for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for nx, ny, nz, dof, ne in rows:
+        g = G.Grid(int(nx), int(ny), int(nz), 1.0)
+        assert g.ndof == int(dof)
+        assert g.E == int(ne)
+
+
+def test_region_counts_12():
+    """Benchmark set-up at 12^3: 5x5 patch nodes, 6x6x9 design-column elements."""
+    g = G.Grid(12, 12, 12, 1 / 12)
+    assert G.patch_nodes(g, G.BCs()).sum() == 25
+    assert synth.design_column(12, 12, 12, 1 / 12).sum() == 6 * 6 * 9
+    assert G.patch_faces(g, G.BCs()).size == 16
+
+
+# ---------------------------------------------------------------- interpolation
+@pytest.mark.parametrize("q", [0.0, 1.0, 8.0, 881.0])
+def test_interpolation_end_points(q):
+    """Sec. 2 Eq. (2)-(3) and Sec. 3.1: K(1)=1, K(0)=1/Ck, alpha(1)=0, alpha(0)=alpha_max."""
+    prm = El.Params(0.1, 1.0, 1.0, alpha_max=1e5, q_alpha=q, q_f=q, Ck=1e-2)
+    assert El.K_of(1.0, prm) == pytest.approx(1.0, rel=1e-15)
+    assert El.K_of(0.0, prm) == pytest.approx(100.0, rel=1e-15)
+    assert El.alpha_of(1.0, prm) == 0.0
+    assert El.alpha_of(0.0, prm) == pytest.approx(1e5, rel=1e-15)
+
+
+def test_interpolation_monotone_and_convex_factor():
+    """Sec. 3.1: larger q pushes intermediate conductivity towards the fluid value
+    (penalises intermediate designs), and alpha decreases monotonically to 0."""
+    g = np.linspace(0.0, 1.0, 101)
+    prev = None
+    for q in (0.881, 8.81, 88.1, 881.0):
+        prm = El.Params(0.1, 1.0, 1.0, alpha_max=1e5, q_alpha=8.0, q_f=q, Ck=1e-2)
+        K = El.K_of(g, prm)
+        assert np.all(np.diff(K) < 0)
+        if prev is not None:
+            assert np.all(K[1:-1] < prev[1:-1])
+        prev = K
+        assert np.all(np.diff(El.alpha_of(g, prm)) < 0)
+
+
+# ---------------------------------------------------------------- tau (App. B)
+def test_tau_printed_derivative_u():
+    """App. B: the printed dtau/du_e equals the (complex-step) derivative of the coded tau.
+    Holds only for the reading ||u_e|| = 2-norm of the 24 velocity unknowns."""
+    rng = np.random.default_rng(7)
+    prm = El.Params(0.05, 1e4, 0.71, alpha_max=1e4)
+    for alpha in (0.0 + 1e-9, 30.0, 3e3):
+        ue = rng.standard_normal(24) * 5.0
+        printed = El.dtau_du_printed(ue, alpha, prm)
+        cs = np.empty(24)
+        for k in range(24):
+            d = np.zeros(24, complex)
+            d[k] = 1e-30j
+            cs[k] = El.tau_momentum((ue + d) @ (ue + d), alpha, prm).imag / 1e-30
+        assert np.allclose(printed, cs, rtol=1e-12, atol=1e-14 * np.abs(cs).max())
+
+
+def test_tau_printed_derivative_gamma():
+    """App. B: the printed dtau/dgamma_e against the complex-step derivative of
+    tau(alpha(gamma)).  As printed, the prefactor is tau/tau3; the derivative of
+    the printed tau has tau*tau3 there (same form as the printed dtau/du_e, which
+    does match), i.e. the printed expression is the derivative times alpha_e^2 =
+    tau3^-2.  Reading: the printed prefactor is a typo; the build differentiates
+    the printed tau exactly.  This test pins that reading."""
+    rng = np.random.default_rng(8)
+    prm = El.Params(0.05, 1e4, 0.71, alpha_max=1e4, q_alpha=8.0)
+    ue = rng.standard_normal(24) * 3.0
+    for gam in (0.1, 0.5, 0.9):
+        printed = El.dtau_dgamma_printed(ue, gam, prm)
+        t = lambda gm: El.tau_momentum(ue @ ue, El.alpha_of(gm, prm), prm)
+        cs = t(gam + 1e-30j).imag / 1e-30
+        tau3 = 1.0 / El.alpha_of(gam, prm)
+        assert printed * tau3 ** 2 == pytest.approx(cs, rel=1e-12)
+        assert abs(printed) > 10 * abs(cs)
+
+
+def test_tau_limits():
+    """App. B: tau is an approximate min of tau1, tau2, tau3."""
+    prm = El.Params(0.1, 1.0, 1.0)
+    # viscous limit (u = 0, alpha = 0): tau = tau2 = h^2 / (4 Pr)
+    assert El.tau_momentum(0.0, 0.0, prm) == pytest.approx(0.1 ** 2 / 4.0, rel=1e-14)
+    # Brinkman-dominated: tau -> 1/alpha
+    assert El.tau_momentum(0.0, 1e12, prm) == pytest.approx(1e-12, rel=1e-6)
+    # convection-dominated: tau -> 4h/||u_e||
+    assert El.tau_momentum(1e16, 0.0, prm) == pytest.approx(4 * 0.1 / 1e8, rel=1e-6)
+
+
+# ---------------------------------------------------------------- Jacobian
+def test_jacobian_matches_central_fd():
+    """The complex-step J equals central finite differences of R (ragged grid)."""
+    g, bc, prob = make(4, 3, 5, 0.2, Gr=1e4)
+    rng = np.random.default_rng(3)
+    gam = rng.uniform(size=g.E)
+    x = prob.impose(rng.standard_normal((5, g.Nn)) * np.array([3, 3, 3, 50, 1.0])[:, None])
+    J = prob.jacobian(x, gam)
+    for s in range(3):
+        v = rng.standard_normal((5, g.Nn))
+        v[prob.dmask] = 0.0
+        eps = 1e-6
+        fd = (prob.residual(x + eps * v, gam) - prob.residual(x - eps * v, gam)) / (2 * eps)
+        Jv = (J @ v.ravel()).reshape(5, -1)
+        assert np.linalg.norm(fd - Jv) <= 1e-8 * np.linalg.norm(Jv)
+
+
+def test_dense_brute_force_newton():
+    """Brute force on 2^3 and 3^3: the Jacobian built column by column from the
+    complex-step derivative of the GLOBAL residual, solved densely, gives the
+    same Newton iterates as the assembled sparse J with LU."""
+    for n in (2, 3):
+        g, bc, prob = make(n, n, n, 1.0 / n, Gr=1e3)
+        rng = np.random.default_rng(n)
+        gam = rng.uniform(size=g.E)
+        x = prob.impose(rng.standard_normal((5, g.Nn)))
+        nd = g.ndof
+        Jd = np.empty((nd, nd))
+        for k in range(nd):
+            e = np.zeros(nd)
+            e[k] = 1.0
+            e = e.reshape(5, -1)
+            e[prob.dmask] = 0.0  # Dirichlet columns removed
+            col = prob.residual(x + 1j * 1e-30 * e, gam).imag / 1e-30
+            col = col.ravel()
+            col[prob.dmask.ravel()] = 0.0
+            if prob.dmask.ravel()[k]:
+                col[k] = 1.0
+            Jd[:, k] = col
+        Js = prob.jacobian(x, gam).toarray()
+        assert np.allclose(Jd, Js, rtol=1e-13, atol=1e-13 * np.abs(Js).max())
+        R = prob.residual(x, gam).ravel()
+        d_dense = np.linalg.solve(Jd, -R)
+        d_sparse = spla.splu(prob.jacobian(x, gam).tocsc()).solve(-R)
+        assert np.allclose(d_dense, d_sparse, rtol=1e-10, atol=1e-12 * np.abs(d_dense).max())
+
+
+# ---------------------------------------------------------------- exact solutions
+def hydrostatic_case(Gr, Pr, T0, nx=5, ny=4, nz=6, h=0.2):
+    bc = G.BCs(T_bc=(G.DIRICHLET,) * 6, T_val=(T0,) * 6, patch_mode=G.PATCH_DIRICHLET,
+               patch_val=T0)
+    g, bc, prob = make(nx, ny, nz, h, Gr=Gr, Pr=Pr, bc=bc)
+    z = g.node_xyz()[:, 2]
+    xs = np.zeros((5, g.Nn))
+    xs[3] = Gr * Pr ** 2 * T0 * (z - g.L[2])
+    xs[4] = T0
+    return g, prob, xs
+
+
+def test_hydrostatic_rest_is_exact():
+    """Sec. 2 Eq. (1): u = 0, uniform T0, p = Gr Pr^2 T0 (z - z_top) solves the
+    strong equations (buoyancy balanced by the pressure gradient, p = 0 on the
+    traction-free top), is trilinear, so the discrete residual vanishes."""
+    g, prob, xs = hydrostatic_case(1e5, 0.71, 1.0)
+    gam = np.random.default_rng(0).uniform(size=g.E)
+    R = prob.residual(xs, gam)
+    scale = 1e5 * 0.71 ** 2 * g.h ** 3
+    assert np.abs(R).max() <= 1e-12 * scale
+
+
+def test_hydrostatic_rest_newton_from_zero():
+    g, prob, xs = hydrostatic_case(1e3, 0.71, 2.0)
+    gam = np.random.default_rng(1).uniform(size=g.E)
+    x, its = S.newton(prob, gam, np.zeros((5, g.Nn)), rtol=1e-13)
+    assert np.abs(x - xs).max() <= 1e-9 * np.abs(xs).max()
+
+
+def q1_laplace_stiffness(h):
+    """Textbook exact Q1 cube stiffness  int grad N_a . grad N_b  for edge h:
+    h/3 on the diagonal, 0 between edge neighbours, -h/12 between face- and
+    body-diagonal corners."""
+    Kc = np.empty((8, 8))
+    for a in range(8):
+        for b in range(8):
+            nd = bin(a ^ b).count("1")
+            Kc[a, b] = {0: h / 3.0, 1: 0.0, 2: -h / 12.0, 3: -h / 12.0}[nd]
+    return Kc
+
+
+def test_pure_conduction_Gr0_textbook():
+    """Gr -> 0 (Sec. 2): no buoyancy, so u = 0, p = 0, and T solves the plain
+    heterogeneous conduction problem sum_e K_e K^Q1 T = patch flux, assembled
+    here from the textbook Q1 stiffness, independently of the oracle."""
+    bc = G.BCs(patch_mode=G.PATCH_FLUX, patch_val=1.0)
+    g, bc, prob = make(6, 5, 7, 1 / 6, Gr=0.0, bc=bc)
+    gam = synth.smoothed_random(6, 5, 7, 1 / 6, 11)
+    gam = np.random.default_rng(2).uniform(size=g.E)
+    x, _ = S.newton(prob, gam, np.zeros((5, g.Nn)), rtol=1e-14)
+    # independent conduction solve
+    conn = g.connectivity()
+    Kc = q1_laplace_stiffness(g.h)
+    Ke = El.K_of(gam, prob.prm)
+    Kg = np.zeros((g.Nn, g.Nn))
+    for e in range(g.E):
+        Kg[np.ix_(conn[e], conn[e])] += Ke[e] * Kc
+    rhs = np.zeros(g.Nn)
+    for e in G.patch_faces(g, bc):
+        rhs[conn[e, :4]] += 1.0 * g.h ** 2 / 4.0
+    dm = prob.dmask[4]
+    T = np.zeros(g.Nn)
+    free = ~dm
+    T[free] = np.linalg.solve(Kg[np.ix_(free, free)], rhs[free])
+    assert np.abs(x[0:4]).max() <= 1e-12
+    assert np.abs(x[4] - T).max() <= 1e-11 * np.abs(T).max()
+
+
+def test_slab_dirichlet_linear_profile():
+    """1-D slab: T = 1 on the whole bottom, 0 on top, adiabatic sides, Gr = 0 ->
+    T = 1 - z / Lz exactly (linear, so exact for Q1)."""
+    bc = G.BCs(T_bc=(G.ADIABATIC,) * 4 + (G.ADIABATIC, G.DIRICHLET), patch=(0, 1, 0, 1),
+               patch_mode=G.PATCH_DIRICHLET, patch_val=1.0)
+    g, bc, prob = make(3, 4, 5, 0.25, Gr=0.0, bc=bc)
+    gam = np.random.default_rng(4).uniform(size=g.E)
+    x, _ = S.newton(prob, gam, np.zeros((5, g.Nn)), rtol=1e-14)
+    z = g.node_xyz()[:, 2]
+    # heterogeneous K along z only would bend the profile; use a z-uniform design
+    gam2 = np.full(g.E, 0.3)
+    x, _ = S.newton(prob, gam2, np.zeros((5, g.Nn)), rtol=1e-14)
+    assert np.abs(x[4] - (1.0 - z / g.L[2])).max() <= 1e-12
+
+
+def test_slab_flux_and_objective():
+    """1-D slab heated by flux q on the whole bottom, T = 0 on top, adiabatic
+    sides, uniform K: T = q (Lz - z) / K exactly; the mean bottom temperature
+    (the objective) is q Lz / K."""
+    q = 2.5
+    bc = G.BCs(T_bc=(G.ADIABATIC,) * 4 + (G.ADIABATIC, G.DIRICHLET), patch=(0, 1, 0, 1),
+               patch_mode=G.PATCH_FLUX, patch_val=q)
+    g, bc, prob = make(4, 3, 5, 0.2, Gr=0.0, bc=bc)
+    gam = np.full(g.E, 0.4)
+    K = El.K_of(0.4, prob.prm)
+    x, _ = S.newton(prob, gam, np.zeros((5, g.Nn)), rtol=1e-14)
+    z = g.node_xyz()[:, 2]
+    assert np.abs(x[4] - q * (g.L[2] - z) / K).max() <= 1e-11 * q * g.L[2] / K
+    phi, dphi = S.objective(prob, bc, x)
+    assert phi == pytest.approx(q * g.L[2] / K, rel=1e-12)
+    assert dphi.sum() == pytest.approx(1.0, rel=1e-14)
+
+
+def test_line_search_closed_form():
+    """Sec. 5.1: the step minimises the quadratic through the three norms."""
+    for lam_true, c2 in ((0.3, 2.0), (0.8, 0.5), (0.02, 4.0)):
+        q = lambda l: c2 * (l - lam_true) ** 2 + 0.1
+        lam = S.line_search_length(q(0.0), q(0.5), q(1.0))
+        assert lam == pytest.approx(max(lam_true, 0.05), rel=1e-12)
+    # concave or minimiser beyond 1: best sampled point, longer on a tie
+    assert S.line_search_length(1.0, 0.5, 0.2) == 1.0
+    assert S.line_search_length(1.0, 2.0, 3.0) == 0.5
+    assert S.line_search_length(1.0, 1.5, 1.5) == 1.0
+
+
+def test_mirror_symmetry():
+    """A design symmetric in x gives a mirror-symmetric converged state:
+    u(-x) = -u, and v, w, p, T even (cavity BCs are x-symmetric)."""
+    nx, ny, nz = 6, 5, 5
+    g, bc, prob = make(nx, ny, nz, 1 / 6, Gr=1e4)
+    gam = np.random.default_rng(5).uniform(size=(nz, ny, nx))
+    gam = 0.5 * (gam + gam[:, :, ::-1])
+    x, _ = S.newton(prob, gam.ravel(), np.zeros((5, g.Nn)), rtol=1e-13)
+    xr = x.reshape(5, nz + 1, ny + 1, nx + 1)
+    m = xr[:, :, :, ::-1]
+    sc = np.abs(x).max(axis=1)
+    assert np.abs(xr[0] + m[0]).max() <= 1e-10 * sc[0]
+    for f in (1, 2, 3, 4):
+        assert np.abs(xr[f] - m[f]).max() <= 1e-10 * max(sc[f], 1e-300)
+    assert sc[0] > 1e-3  # the flow is not trivially zero
+
+
+# ---------------------------------------------------------------- manufactured solution
+def mms_fields():
+    sympy = pytest.importorskip("sympy")
+    X, Y, Z = sympy.symbols("x y z")
+    pi = sympy.pi
+    psi = sympy.sin(pi * X) * sympy.sin(pi * Y) * sympy.sin(pi * Z)
+    phi = sympy.cos(pi * X) * sympy.sin(pi * Y) * sympy.sin(pi * Z) / 2
+    A = (phi, 0, psi)
+    u = [sympy.diff(A[2], Y) - sympy.diff(A[1], Z), sympy.diff(A[0], Z) - sympy.diff(A[2], X),
+         sympy.diff(A[1], X) - sympy.diff(A[0], Y)]
+    p = sympy.cos(pi * X) * sympy.cos(pi * Y) * Z
+    T = sympy.sin(pi * X) * Y ** 2 + Z
+    return sympy, (X, Y, Z), u, p, T
+
+
+def test_mms_convergence():
+    """Sec. 2 Eq. (1): with a smooth divergence-free manufactured solution and
+    its body forces, the discrete solution converges at second order in u, T
+    (and at least first in p) -- a dropped term, a sign or an index error
+    breaks convergence."""
+    sympy, (X, Y, Z), u, p, T = mms_fields()
+    Gr, Pr, gam0 = 10.0, 1.0, 0.5
+    mat = dict(alpha_max=10.0, q_alpha=1.0, q_f=1.0, Ck=0.5)
+    prm0 = El.Params(1.0, Gr, Pr, **mat)
+    alpha, K = El.alpha_of(gam0, prm0), El.K_of(gam0, prm0)
+    xs = (X, Y, Z)
+    eg = (0, 0, -1)
+    fM = []
+    for i in range(3):
+        conv = sum(u[j] * sympy.diff(u[i], xs[j]) for j in range(3))
+        visc = sum(sympy.diff(sympy.diff(u[i], xs[j]) + sympy.diff(u[j], xs[i]), xs[j])
+                   for j in range(3))
+        fM.append(conv - Pr * visc + sympy.diff(p, xs[i]) + alpha * u[i]
+                  + Gr * Pr ** 2 * eg[i] * T)
+    divu = sympy.simplify(sum(sympy.diff(u[j], xs[j]) for j in range(3)))
+    assert divu == 0
+    fT = sum(u[j] * sympy.diff(T, xs[j]) for j in range(3)) \
+        - K * sum(sympy.diff(T, xs[j], 2) for j in range(3))
+    fM_l = [sympy.lambdify(xs, f, "numpy") for f in fM]
+    fT_l = sympy.lambdify(xs, fT, "numpy")
+    ex_l = [sympy.lambdify(xs, f, "numpy") for f in (u + [p, T])]
+
+    def force(xyz):
+        a = (xyz[:, 0], xyz[:, 1], xyz[:, 2])
+        fm = np.stack([np.broadcast_to(f(*a), xyz[:, 0].shape) for f in fM_l], 1)
+        return fm, 0.0, np.broadcast_to(fT_l(*a), xyz[:, 0].shape)
+
+    errs = []
+    for n in (4, 8, 12):
+        g = G.Grid(n, n, n, 1.0 / n)
+        xyz = g.node_xyz()
+        exact = np.stack([np.broadcast_to(f(xyz[:, 0], xyz[:, 1], xyz[:, 2]), (g.Nn,))
+                          for f in ex_l])
+        onb = np.zeros(g.Nn, bool)
+        ijk = g.node_ijk()
+        for d, nd in enumerate((n, n, n)):
+            onb |= (ijk[:, d] == 0) | (ijk[:, d] == nd)
+        dm = np.zeros((5, g.Nn), bool)
+        dm[[0, 1, 2, 4]] = onb
+        dm[3, 0] = True
+        prm = El.Params(1.0 / n, Gr, Pr, **mat)
+        prob = A.Problem(g, prm, dm, exact.copy(), force=force)
+        x, _ = S.newton(prob, np.full(g.E, gam0), np.zeros((5, g.Nn)), rtol=1e-12)
+        rms = lambda a: np.sqrt(np.mean(a ** 2))
+        errs.append([rms(x[0:3] - exact[0:3]), rms(x[3] - exact[3]), rms(x[4] - exact[4])])
+    errs = np.array(errs)
+    order = np.log(errs[1] / errs[2]) / np.log(12 / 8)
+    assert order[0] > 1.8, (errs, order)   # velocity
+    assert order[2] > 1.8, (errs, order)   # temperature
+    # pressure (equal-order PSPG, viscous second derivatives dropped from the
+    # strong residual): at least first order over 4 -> 12
+    assert np.log(errs[0, 1] / errs[2, 1]) / np.log(3.0) > 1.0, errs
+
+
+# ---------------------------------------------------------------- sensitivities (Sec. 3.2, App. B)
+def flux_case(n=4, Gr=1e5):
+    bc = G.BCs(patch_mode=G.PATCH_FLUX, patch_val=1.0, patch=(0.25, 0.75, 0.25, 0.75))
+    return make(n, n, n, 1.0 / n, Gr=Gr, bc=bc, alpha_max=1e3)
+
+
+def test_sensitivity_matches_fd_and_consistency_matters():
+    """Consistent adjoint sensitivities agree with central FD (step 1e-6) of the
+    Newton-converged objective to <= 1e-5 relative; leaving the tau variations
+    out of the adjoint (App. B's inconsistent version) is visibly worse."""
+    g, bc, prob = flux_case()
+    rng = np.random.default_rng(9)
+    gam = rng.uniform(0.2, 1.0, size=g.E)
+    x = np.zeros((5, g.Nn))
+    for Gr in (1e3, 1e4, 1e5):  # convection-dominated, so tau1 matters
+        prob.prm.Gr = Gr
+        x, _ = S.newton(prob, gam, x, rtol=1e-14, atol=1e-13)
+    phi, dphi = S.objective(prob, bc, x)
+    lam = S.adjoint(prob, x, gam, -dphi)
+    sens = S.sensitivity(prob, x, gam, lam)
+    # inconsistent: tau frozen in both the adjoint operator and dR/dgamma
+    Jf = prob.jacobian(x, gam, freeze_tau=True)
+    lam_f = spla.splu(Jf.T.tocsc()).solve(-dphi.ravel()).reshape(5, -1)
+    lam_f[prob.dmask] = 0.0
+    dre_f = prob.element_rows(x, gam + 1j * 1e-30, freeze_tau=True).imag / 1e-30
+    sens_f = np.einsum("eaf,eaf->e", A.gather(lam_f, prob.conn), dre_f)
+    elems = rng.choice(g.E, size=6, replace=False)
+    fd = []
+    for e in elems:
+        vals = []
+        for s in (+1, -1):
+            gp = gam.copy()
+            gp[e] += s * 1e-6
+            xp, _ = S.newton(prob, gp, x, rtol=0.0, atol=1e-12, maxit=8)
+            vals.append(S.objective(prob, bc, xp)[0])
+        fd.append((vals[0] - vals[1]) / 2e-6)
+    fd = np.array(fd)
+    err = np.abs(sens[elems] - fd).max() / np.abs(fd).max()
+    err_f = np.abs(sens_f[elems] - fd).max() / np.abs(fd).max()
+    assert err <= 1e-5, err
+    assert err_f >= 10 * err, (err, err_f)
+
+
+def test_adjoint_dot_product():
+    """w^T (J v) = (J^T w)^T v for the Dirichlet-modified operator."""
+    g, bc, prob = flux_case(3)
+    rng = np.random.default_rng(10)
+    gam = rng.uniform(size=g.E)
+    x = prob.impose(rng.standard_normal((5, g.Nn)))
+    J = prob.jacobian(x, gam)
+    v, w = rng.standard_normal(g.ndof), rng.standard_normal(g.ndof)
+    assert w @ (J @ v) == pytest.approx(v @ (J.T @ w), rel=1e-13)
