@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark of the matrix-free Jacobian-vector product and of the state +
+adjoint solves, on synthetic heat-sink cavity workloads.
+
+Default workload: 64^3 elements, 4x4 vertical fins design (seeded), Gr = 1e4,
+Pr = 0.71 (the plain-FP64 GPU configuration).  One timed step is one batch of
+16 J v applications at the converged state with 16 seeded random directions;
+the reported value is J v throughput in GDOF/s (all 5 Nn unknowns per
+application).  The same run also times, outside the J v region, the full hot
+path once per precision: Newton state solve to 1e-8, adjoint solve to 1e-8 and
+the element sensitivities, FP32-mixed against plain FP64.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload NAME] [--prec f64|f32] [--no-solve]
+N > 1 runs under torchrun: every rank solves its own copy (replicas; the path
+does not shard) and rank 0 prints the line.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+NAPPLY = 16  # J v applications per step
+# Operation counts per element (one +, -, * or / = 1 flop; an FMA = 2), of the
+# element routines in csrc/nc_element.cuh, counted by instantiating them with a
+# counting number type.
+FLOPS_PER_ELEM = {"residual": 6482, "jvp": 10386, "jtvp": 9938, "diag": 9093, "sens": 8146}
+# ALU peaks (whole GPU): FP32 = 152 SM x 128 lanes x 2 flop x 2.07 GHz; FP64 = the
+# GB300's nominal 1.25 TFLOP/s (equal to our FMA-chain probe on the box: 78.5 and
+# 1.25 TFLOP/s measured).
+ALU_PEAK_TFLOPS = {"f32": 152 * 128 * 2 * 2.07e9 / 1e12, "f64": 1.25}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fins64_gr1e4")
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--no-solve", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+    return rank, world
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.samples, self.stop_ev = index, [], threading.Event()
+
+    def _run(self):
+        while not self.stop_ev.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([s.strip() for s in out.split(",")])
+            except Exception:
+                pass
+            self.stop_ev.wait(0.2)
+
+    def __enter__(self):
+        self.t = threading.Thread(target=self._run, daemon=True)
+        self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        self.stop_ev.set()
+        self.t.join(timeout=6)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 2 + i and s[2 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "MEASURED_PEAKS.json"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0}, "fallback 6.8 TB/s"
+
+
+# ---------------------------------------------------------------------------------- ours
+def run_ours(args, rank, world):
+    import torch
+    from paper_1508_04596_gb300 import nc, synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda")
+    cfg = synth.WORKLOADS[args.workload]
+    n = (cfg["nx"], cfg["ny"], cfg["nz"])
+    prob = nc.Problem.from_workload(args.workload)
+    gam64 = torch.tensor(synth.design(args.workload), dtype=torch.float64, device=dev)
+    ndof = prob.ndof
+    stream = torch.cuda.current_stream()
+    extra = {}
+
+    # --- full hot path once per precision: state, adjoint, sensitivity
+    x = torch.zeros(ndof, dtype=torch.float64, device=dev)
+    solve = {}
+    if not args.no_solve:
+        xs = {}
+        for mode, mixed in (("mixed", 1), ("fp64", 0)):
+            xm = torch.zeros(ndof, dtype=torch.float64, device=dev)
+            opts = nc.default_opts(mixed=mixed, rtol_newton=1e-8, ramp_steps=2)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, inf = prob.newton_solve(gam64, xm, opts, check=False)
+            torch.cuda.synchronize()
+            ts = time.perf_counter() - t0
+            phi, dphi = prob.objective(xm)
+            t0 = time.perf_counter()
+            lam, ainf = prob.adjoint_solve(xm, gam64, -dphi, opts=opts, check=False)
+            sens = prob.sensitivity(xm, gam64, lam)
+            torch.cuda.synchronize()
+            ta = time.perf_counter() - t0
+            xs[mode] = (xm, sens)
+            solve[mode] = {"state_s": round(ts, 4), "adjoint_plus_sens_s": round(ta, 4),
+                           "newton_its": inf["newton_its"], "lin_its": inf["lin_its_total"],
+                           "state_status": inf["status"], "adjoint_lin_its": ainf["lin_its_total"],
+                           "adjoint_status": ainf["status"],
+                           "rel_res_final": inf["res_final"] / max(inf["res0"], 1e-300),
+                           "phi": phi}
+        xa, sa = xs["mixed"]
+        xb, sb = xs["fp64"]
+        solve["mixed_vs_fp64_state_rel"] = float(torch.linalg.norm(xa - xb) / torch.linalg.norm(xb))
+        solve["mixed_vs_fp64_sens_rel"] = float(torch.linalg.norm(sa - sb) / torch.linalg.norm(sb))
+        solve["speedup_state_adjoint"] = round(
+            (solve["fp64"]["state_s"] + solve["fp64"]["adjoint_plus_sens_s"])
+            / (solve["mixed"]["state_s"] + solve["mixed"]["adjoint_plus_sens_s"]), 3)
+        x = xb if solve["fp64"]["state_status"] == "NC_OK" else xa
+    else:
+        x = torch.tensor(synth.random_state(*n, 1, (0.5, 0.5, 0.5, 50, 1)).ravel(),
+                         dtype=torch.float64, device=dev)
+        prob.impose_dirichlet(x)
+
+    # --- J v throughput
+    dt = torch.float64 if args.prec == "f64" else torch.float32
+    xj, gj = x.to(dt), gam64.to(dt)
+    g = torch.Generator(device="cpu").manual_seed(1234)
+    V = torch.randn(NAPPLY, ndof, generator=g, dtype=torch.float64).to(dev, dt)
+    out = torch.empty_like(xj)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+
+    def step():
+        for i in range(NAPPLY):
+            prob.jvp(xj, gj, V[i], out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(torch.cuda.current_device()) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    t_step = float(np.sum(ms)) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = tt.item()
+        dist.barrier()
+    value = world * NAPPLY * ndof / (t_step * 1e-3) / 1e9
+
+    # --- roofline of the dominant kernel (the J v element kernel + owner gather)
+    flops = FLOPS_PER_ELEM["jvp"] * prob.E
+    t_apply = t_step / NAPPLY * 1e-3
+    achieved = flops / t_apply / 1e12
+    peak = ALU_PEAK_TFLOPS[args.prec]
+    roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "kernel": "k_elem_lin<%s> + k_gather" % ("double" if dt == torch.float64 else "float"),
+            "peak_source": "ALU unit counts x 2.07 GHz (FP32) / nominal FP64 rate"}
+
+    # --- end to end through the C ABI with host buffers
+    xh = xj.cpu().pin_memory()
+    gh = gj.cpu().pin_memory()
+    Vh = V.cpu().pin_memory()
+    outh = torch.empty((NAPPLY, ndof), dtype=dt).pin_memory()
+    xd, gd, Vd, od = torch.empty_like(xj), torch.empty_like(gj), torch.empty_like(V), torch.empty_like(V)
+
+    def e2e_step():
+        xd.copy_(xh, non_blocking=True)
+        gd.copy_(gh, non_blocking=True)
+        Vd.copy_(Vh, non_blocking=True)
+        for i in range(NAPPLY):
+            prob.jvp(xd, gd, Vd[i], od[i])
+        outh.copy_(od, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k2 = max(3, args.steps // 4)
+    e0.record(stream)
+    for _ in range(k2):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = e0.elapsed_time(e1) / k2
+    esz = xj.element_size()
+    h2d = (xj.numel() + gj.numel() + V.numel()) * esz
+    d2h = V.numel() * esz
+    e2e = {"value": round(world * NAPPLY * ndof / (t_e2e * 1e-3) / 1e9, 4), "unit": "GDOF/s",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # --- other operators at the same state (for context)
+    ops = {}
+    for name, fn in (("residual", lambda: prob.residual(xj, gj, out)),
+                     ("jtvp", lambda: prob.jtvp(xj, gj, V[0], out)),
+                     ("diag", lambda: prob.diag(xj, gj, out))):
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(5):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / 5
+        ops[name] = {"ms": round(t, 4), "gdofs": round(ndof / t / 1e6, 3),
+                     "alu_frac": round(FLOPS_PER_ELEM[name] * prob.E / (t * 1e-3) / 1e12 / peak, 4)}
+    extra["operators"] = ops
+    if solve:
+        extra["solve"] = solve
+
+    if rank != 0:
+        return None
+    cpu = cpu_baseline(args.workload) if world == 1 else None
+    line = {"metric": "J·v GDOF/s and state+adjoint solve time, FP32-mixed vs FP64 at 1e-8 rel",
+            "value": round(value, 4), "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+            "config": {"workload": args.workload, "grid": list(n), "dof": ndof,
+                       "Gr": cfg["Gr"], "Pr": cfg["Pr"], "jv_per_step": NAPPLY,
+                       "l2": "flushed between steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single-gpu"},
+            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": 2 * NAPPLY * args.steps,
+            "roofline": roof, "cpu_baseline": cpu}
+    line.update(extra)
+    return line
+
+
+# ------------------------------------------------------------------------- CPU oracle
+def oracle_sample(workload, layers=4):
+    """The bottom `layers` element layers of the workload (a bounded sample)."""
+    from paper_1508_04596_gb300 import synth
+    from tests.helpers import oracle_problem, random_bc_state
+    cfg = synth.WORKLOADS[workload]
+    nx, ny = cfg["nx"], cfg["ny"]
+    nz = min(layers, cfg["nz"])
+    prob, _ = oracle_problem(nx, ny, nz, cfg["h"], cfg["Gr"], cfg["Pr"], patch_mode=cfg["patch"])
+    gam = synth.design(workload).reshape(cfg["nz"], ny, nx)[:nz].ravel()
+    x = random_bc_state(prob, 5)
+    return prob, gam, x
+
+
+def cpu_baseline(workload, reps=16):
+    """Oracle J v as an assembled CSR SpMV (scipy, one thread) on a bounded sample."""
+    prob, gam, x = oracle_sample(workload)
+    t0 = time.perf_counter()
+    J = prob.jacobian(x, gam)
+    t_asm = time.perf_counter() - t0
+    v = np.random.default_rng(0).standard_normal(prob.g.ndof)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        J @ v
+    t = (time.perf_counter() - t0) / reps
+    return {"value": round(prob.g.ndof / t / 1e9, 5), "unit": "GDOF/s", "cores": 1,
+            "kind": "oracle",
+            "sample": "%dx%dx%d bottom layers of %s: complex-step CSR assembly %.1f s, then %d SpMV"
+                      % (prob.g.nx, prob.g.ny, prob.g.nz, workload, t_asm, reps)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    prob, gam, x = oracle_sample(args.workload)
+    t0 = time.perf_counter()
+    J = prob.jacobian(x, gam)
+    t_asm = time.perf_counter() - t0
+    rng = np.random.default_rng(1234)
+    V = rng.standard_normal((NAPPLY, prob.g.ndof))
+
+    def step():
+        for i in range(NAPPLY):
+            J @ V[i]
+
+    for _ in range(args.warmup):
+        step()
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        ts.append(time.perf_counter() - t0)
+    t = float(np.mean(ts))
+    value = NAPPLY * prob.g.ndof / t / 1e9
+    sample = ("%dx%dx%d bottom layers of %s (assembly %.1f s, untimed), %d SpMV per step"
+              % (prob.g.nx, prob.g.ny, prob.g.nz, args.workload, t_asm, NAPPLY))
+    return {"impl": "reference", "metric": "J·v GDOF/s and state+adjoint solve time, FP32-mixed vs FP64 at 1e-8 rel",
+            "value": round(value, 5), "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "jv_per_step": NAPPLY},
+            "cpu_baseline": {"value": round(value, 5), "unit": "GDOF/s", "cores": 1,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 5), "unit": "GDOF/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world = dist_init(args)
+    line = run_reference(args, rank, world) if args.impl == "reference" else run_ours(args, rank, world)
+    if rank == 0 and line is not None:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/* nc.h -- C ABI of libnc: a single-GPU (GB300, sm_103a) solver for the stabilised
+ * Q1-Q1 natural-convection equations used in "Large scale three-dimensional
+ * topology optimisation of heat sinks cooled by natural convection"
+ * (Alexandersen, Sigmund, Aage).
+ *
+ * Problem (Sec. 2, Eq. 1a-c), dimensionless:
+ *   u.grad u - Pr div(grad u + grad u^T) + grad p = -alpha(gamma) u - Gr Pr^2 e^g T
+ *   div u = 0
+ *   u.grad T - div(K(gamma) grad T) = s
+ * with the design interpolations of Sec. 3.1 (Eq. 7-8), discretised with
+ * stabilised trilinear hexahedra on a structured grid (Sec. 4, App. B).
+ *
+ * Conventions shared by every call:
+ *  - Grid: nx*ny*nz cubic elements of edge h; node n = i + (nx+1)(j + (ny+1)k),
+ *    element e = i + nx(j + ny k); z is vertical.
+ *  - State and vector arrays: structure of arrays [5][Nn] (u, v, w, p, T), Nn the
+ *    node count; design and element arrays: [E].
+ *  - Array arguments are DEVICE pointers owned by the caller, unless a name ends
+ *    in _host.  Element type: double for NC_FP64, float for NC_FP32.
+ *  - Calls enqueue work on `stream` (a cudaStream_t; NULL = legacy default stream)
+ *    and return without synchronising, except where a call documents a host result.
+ *  - Inputs are never modified, except arguments named *_inout.
+ *  - Errors: every call returns an nc_status; nc_last_error(ctx) gives a message.
+ *    The library never aborts and never prints.
+ *  - Dirichlet rows: the residual row of a Dirichlet unknown is x - x_D; the
+ *    Jacobian is blockdiag(J_II, I): Dirichlet columns are removed from the
+ *    interior rows and Dirichlet rows are identity rows, so (J v)_D = v_D and
+ *    (J^T w)_D = w_D.
+ */
+#ifndef NC_H
+#define NC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nc_ctx nc_ctx;
+
+typedef enum {
+  NC_OK = 0,
+  NC_ERR_ARG = 1,      /* invalid argument (sizes, pointers, options) */
+  NC_ERR_CUDA = 2,     /* a CUDA runtime call failed */
+  NC_ERR_OOM = 3,      /* device allocation failed */
+  NC_ERR_NAN = 4,      /* a non-finite value appeared in a norm */
+  NC_ERR_MAXIT = 5,    /* iteration limit reached before the tolerance */
+  NC_ERR_DIVERGED = 6  /* Newton line search found no decrease */
+} nc_status;
+
+typedef enum { NC_FP64 = 0, NC_FP32 = 1 } nc_prec;
+
+enum { NC_VEL_NOSLIP = 0, NC_VEL_FREE = 1, NC_VEL_SYMMETRY = 2 };
+enum { NC_T_ADIABATIC = 0, NC_T_DIRICHLET = 1 };
+enum { NC_PATCH_NONE = 0, NC_PATCH_DIRICHLET = 1, NC_PATCH_FLUX = 2 };
+
+/* Physical and discretisation parameters (Sec. 2, Sec. 3.1, Sec. 6.1). */
+typedef struct {
+  int nx, ny, nz;     /* elements per direction, >= 1 */
+  double h;           /* element edge length, > 0 */
+  double Gr, Pr;      /* Grashof and Prandtl numbers (Sec. 2) */
+  double alpha_max;   /* Brinkman impermeability of solid (Sec. 3.1, Eq. 8) */
+  double q_alpha;     /* convexity of the alpha interpolation (Eq. 8) */
+  double q_f;         /* convexity of the conductivity interpolation (Eq. 7) */
+  double Ck;          /* k_f / k_s (Sec. 2); K(solid) = 1/Ck */
+  double g_dir[3];    /* unit gravity direction e^g, e.g. (0,0,-1) */
+} nc_params;
+
+/* Boundary conditions per face, order (-x, +x, -y, +y, -z, +z).
+ * Velocity: NC_VEL_NOSLIP (u = 0), NC_VEL_FREE (traction-free, natural),
+ * NC_VEL_SYMMETRY (normal component 0).  Temperature: NC_T_ADIABATIC or
+ * NC_T_DIRICHLET with value T_val[face].  A rectangular patch of the bottom face,
+ * patch = {x0, x1, y0, y1} as fractions of the domain width (closed interval,
+ * tolerance 1e-12 of the domain size), is either held at T = patch_val
+ * (NC_PATCH_DIRICHLET) or heated by the inward flux q = patch_val
+ * (NC_PATCH_FLUX, applied on the bottom faces whose four nodes lie in the
+ * patch).  Dirichlet temperature precedence on shared nodes: -x, +x, -y, +y
+ * faces, then the patch, then -z, then +z.  p_pin >= 0 pins the pressure of that
+ * node to 0 (closed cavities); -1 for none. */
+typedef struct {
+  int vel_bc[6];
+  int T_bc[6];
+  double T_val[6];
+  double patch[4];
+  int patch_mode;
+  double patch_val;
+  long long p_pin;
+} nc_bcs;
+
+/* Sizes of the discrete problem, computed without allocating anything.
+ * Any output pointer may be NULL.  Returns NC_ERR_ARG for invalid sizes. */
+nc_status nc_sizes(const nc_params* prm, long long* n_nodes, long long* n_elems,
+                   long long* n_dof);
+
+/* Create a context on the current CUDA device: boundary-condition flags, the
+ * multigrid level hierarchy (halving while every dimension stays even and at
+ * least 2 elements remain) and all operator workspace are allocated here.
+ * Krylov workspace is allocated at the first solve (sized by its restart).
+ * On failure *out is NULL and the status says why. */
+nc_status nc_setup(const nc_params* prm, const nc_bcs* bcs, nc_ctx** out);
+
+/* Release every device allocation of the context.  NULL is accepted. */
+void nc_destroy(nc_ctx* ctx);
+
+/* Message of the last failed call on ctx (empty string if none; never NULL). */
+const char* nc_last_error(const nc_ctx* ctx);
+
+/* Static text for a status code. */
+const char* nc_status_string(int status);
+
+/* Per-node boundary flags computed by nc_setup, copied to host memory:
+ * bit f (0..4) set if unknown f of the node is Dirichlet.  flags_host has Nn
+ * bytes.  Synchronous. */
+nc_status nc_bc_flags(nc_ctx* ctx, unsigned char* flags_host);
+
+/* Optional element heat source s_e (Sec. 2, the s0 of the paper on the subdomain
+ * omega), device array [E] of doubles copied into the context; NULL clears it.
+ * Synchronous with respect to the given stream. */
+nc_status nc_set_source(nc_ctx* ctx, const double* source_e, void* stream);
+
+/* x_inout[D] := x_D (the Dirichlet values of the boundary conditions). */
+nc_status nc_impose_dirichlet(nc_ctx* ctx, void* x_inout, int prec, void* stream);
+
+/* Residual R(x, gamma) of the stabilised weak form (Sec. 4; App. B) plus the
+ * patch flux term, Dirichlet rows x - x_D.  x, r: [5][Nn]; gamma: [E] with
+ * gamma = 1 fluid, 0 solid (Sec. 3.1). */
+nc_status nc_residual(nc_ctx* ctx, const void* x, const void* gamma, void* r, int prec,
+                      void* stream);
+
+/* Jv = J(x, gamma) v, the consistent Jacobian including the variation of the
+ * stabilisation parameters with the velocity (App. B, dtau/du_e), matrix-free. */
+nc_status nc_jvp(nc_ctx* ctx, const void* x, const void* gamma, const void* v, void* Jv,
+                 int prec, void* stream);
+
+/* JTw = J(x, gamma)^T w (the adjoint operator of Sec. 3.2), matrix-free. */
+nc_status nc_jtvp(nc_ctx* ctx, const void* x, const void* gamma, const void* w, void* JTw,
+                  int prec, void* stream);
+
+/* d = diag(J(x, gamma)) (1 on Dirichlet rows): the Jacobi scaling of the
+ * multigrid smoother (Sec. 5.2). */
+nc_status nc_diag(nc_ctx* ctx, const void* x, const void* gamma, void* d, int prec,
+                  void* stream);
+
+/* Objective: mean temperature of the bottom patch, Phi = (1/|Gamma_p|) int T dA
+ * (the patch analogue of the thermal compliance of Sec. 3.2).  FP64 only.
+ * phi_host receives Phi (the call synchronises the stream); dphidx, if not NULL,
+ * receives dPhi/dx as [5][Nn]. */
+nc_status nc_objective(nc_ctx* ctx, const double* x, double* phi_host, double* dphidx,
+                       void* stream);
+
+/* Design sensitivities dPhi/dgamma_e = lambda^T dR/dgamma_e (Sec. 3.2, with
+ * dtau/dgamma_e of App. B and dtau_T/dK_e), Dirichlet rows excluded, for the
+ * adjoint lambda of J^T lambda = -dPhi/dx.  Output [E].  FP64 only. */
+nc_status nc_sensitivity(nc_ctx* ctx, const double* x, const double* gamma,
+                         const double* lambda, double* dphidgamma, void* stream);
+
+/* Solver options.  rtol_newton: stop when ||R|| <= rtol_newton ||R_0|| (Sec. 5.1);
+ * rtol_lin: FGMRES relative tolerance per linear solve (Sec. 5.2); max_newton,
+ * max_lin (total FGMRES iterations per linear solve), restart (FGMRES restart,
+ * <= 64); mg_levels: multigrid levels to use (0 = all); smooth_its: Jacobi-GMRES
+ * smoothing iterations per pre/post step; coarse_its: Jacobi-GMRES iterations on
+ * the coarsest level; mixed: 1 = Jacobian products, smoother and coarse levels
+ * in FP32 inside FP64 Newton / refinement, 0 = everything FP64; ramp_steps: on
+ * Newton failure from the given start, retry with the buoyancy (Gr) ramped up
+ * in this many geometric steps (0 = no ramping; the paper ramps the heat load,
+ * Sec. 5.1). */
+typedef struct {
+  double rtol_newton, rtol_lin;
+  int max_newton, max_lin, restart;
+  int mg_levels, smooth_its, coarse_its;
+  int mixed;
+  int ramp_steps;
+} nc_solve_opts;
+
+/* Per-solve report (Sec. 6.2 reports Newton and linear iteration counts). */
+typedef struct {
+  int newton_its, lin_its_total, status;
+  double res0, res_final, seconds;
+  double res_hist[64];
+} nc_solve_info;
+
+/* Fill opts with defaults (rtol_newton 1e-8, rtol_lin 1e-5, max_newton 30,
+ * max_lin 200, restart 30, all levels, smooth_its 2, coarse_its 30, mixed 1,
+ * ramp_steps 0). */
+void nc_default_opts(nc_solve_opts* opts);
+
+/* Damped Newton (Sec. 5.1) on R(x, gamma) = 0 from x_inout (Dirichlet values
+ * imposed first), step length from the quadratic fit of ||R|| at 0, 1/2 and 1
+ * of the Newton step; each linear system by FGMRES preconditioned with a
+ * geometric multigrid V-cycle whose smoother is Jacobi-preconditioned GMRES
+ * (Sec. 5.2).  x_inout: [5][Nn] FP64, gamma: [E] FP64.  info may be NULL.
+ * Synchronous. */
+nc_status nc_newton_solve(nc_ctx* ctx, const double* gamma, double* x_inout,
+                          const nc_solve_opts* opts, nc_solve_info* info, void* stream);
+
+/* Adjoint solve J(x, gamma)^T lambda = rhs (Sec. 3.2) by FGMRES + multigrid on the
+ * transposed operators, inside FP64 iterative refinement until
+ * ||rhs - J^T lambda|| <= rtol_newton ||rhs||.  All FP64 [5][Nn].  Synchronous. */
+nc_status nc_adjoint_solve(nc_ctx* ctx, const double* x, const double* gamma,
+                           const double* rhs, double* lambda_out, const nc_solve_opts* opts,
+                           nc_solve_info* info, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NC_H */

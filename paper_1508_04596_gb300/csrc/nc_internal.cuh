@@ -1,0 +1,156 @@
+// Internal structures and kernel launchers of libnc (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/nc.h"
+#include "nc_element.cuh"
+
+namespace nc {
+
+constexpr int NF = 5;
+constexpr int MAX_LEVELS = 16;
+constexpr int RED_THREADS = 256;
+constexpr int RED_BLOCKS_MAX = 608;  // 4 x 152 SMs
+constexpr int MAX_RESTART = 64;
+
+// Geometry and boundary data of one grid level, passed to kernels by value.
+struct LevelDev {
+  int nx, ny, nz;
+  long long Nn, E;
+  double h;
+  const uint8_t* flag;  // per node: bits 0..4 Dirichlet field mask, bits 5..7 T value index
+  double tval[8];       // Dirichlet temperature values by index
+  int patch_mode;       // NC_PATCH_*
+  int pi0, pi1, pj0, pj1;  // patch node index range on the bottom face (inclusive)
+  double q;             // patch flux (NC_PATCH_FLUX)
+};
+
+template <typename R>
+struct Vec {
+  R* p = nullptr;
+};
+
+// Per level, per precision buffers used by the multigrid cycle.
+template <typename R>
+struct LevelBuf {
+  R* x = nullptr;      // linearisation state (levels >= 1; level 0 points elsewhere)
+  R* gam = nullptr;    // design
+  R* src = nullptr;    // element source (may be null)
+  R* diag = nullptr;   // diag(J)
+  R* b = nullptr;      // cycle right-hand side
+  R* z = nullptr;      // cycle solution
+  R* r = nullptr;      // temporary residual
+  R* t = nullptr;      // temporary
+  R* V = nullptr;      // smoother Krylov basis, (ks+1) vectors
+  R* H = nullptr;      // unused for R = float (scalars are kept in double, see Hd)
+  double* Hd = nullptr;  // device scalars: Hessenberg (MAX_RESTART+1)^2, y, beta, norms
+  int ks = 0;
+  bool ext = false;    // x and gam point to caller/Newton arrays (level 0, FP64)
+};
+
+struct Level {
+  LevelDev d;
+  uint8_t* flag = nullptr;
+  ElemConst<double> c64;
+  ElemConst<float> c32;
+  LevelBuf<double> f64;
+  LevelBuf<float> f32;
+};
+
+struct Krylov {
+  int m = 0;
+  double* V = nullptr;   // (m+1) x ndof
+  double* Z = nullptr;   // m x ndof
+  double* w = nullptr;
+  double* hcol = nullptr;  // device, 2*(m+2)
+  double* y = nullptr;     // device, m
+};
+
+}  // namespace nc
+
+struct nc_ctx {
+  nc_params prm;
+  nc_bcs bcs;
+  std::vector<nc::Level> lv;
+  double* Y = nullptr;        // element output scratch, 40 * E(level 0) doubles
+  double* partial = nullptr;  // reduction partials, (MAX_RESTART+2) * RED_BLOCKS_MAX doubles
+  double* dscal = nullptr;    // device scalars for reductions (MAX_RESTART+2)
+  double* src64 = nullptr;    // element source (level 0), FP64
+  nc::Krylov kry;
+  double* tmp64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // FP64 [5][Nn]
+  float* tmp32[2] = {nullptr, nullptr};
+  int ws_ks = 0;              // smoother workspace size allocated
+  std::string err;
+};
+
+namespace nc {
+
+// ---- element operators (nc_kernels.cu); Y is scratch of 40*E elements of R
+template <typename R>
+void op_residual(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam, const R* src,
+                 R* r, R* Y, cudaStream_t s);
+template <typename R>
+void op_jvp(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam, const R* src,
+            const R* v, R* out, R* Y, cudaStream_t s);
+template <typename R>
+void op_jtvp(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam, const R* src,
+             const R* w, R* out, R* Y, cudaStream_t s);
+template <typename R>
+void op_diag(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam, const R* src,
+             R* out, R* Y, cudaStream_t s);
+void op_sens(const LevelDev& d, const ElemConst<double>& c, const double* x, const double* gam,
+             const double* src, const double* lam, double* out, cudaStream_t s);
+template <typename R>
+void op_impose(const LevelDev& d, R* x, cudaStream_t s);
+template <typename R>
+void op_mask(const LevelDev& d, R* x, cudaStream_t s);  // zero Dirichlet entries
+void op_objective_grad(const LevelDev& d, double* dphidx, cudaStream_t s);
+double patch_area(const LevelDev& d);
+
+// ---- transfers
+template <typename R>
+void op_restrict(const LevelDev& fine, const R* rf, const LevelDev& coarse, R* rc, cudaStream_t s);
+template <typename R>
+void op_prolong_add(const LevelDev& coarse, const R* zc, const LevelDev& fine, R* zf,
+                    cudaStream_t s);
+template <typename R>
+void op_inject(const LevelDev& fine, const R* xf, const LevelDev& coarse, R* xc, cudaStream_t s);
+template <typename R>
+void op_coarsen_elem(const LevelDev& fine, const R* gf, const LevelDev& coarse, R* gc,
+                     cudaStream_t s);
+
+// ---- vector kernels (deterministic fixed-partition reductions)
+template <typename Rd, typename Rs>
+void vcast(long long n, const Rs* x, Rd* y, cudaStream_t s);
+template <typename R>
+void vcopy(long long n, const R* x, R* y, cudaStream_t s);
+template <typename R>
+void vzero(long long n, R* x, cudaStream_t s);
+template <typename R>
+void vaxpy(long long n, R a, const R* x, R* y, cudaStream_t s);  // y += a x
+template <typename R>
+void vxpay(long long n, const R* x, R a, R* y, cudaStream_t s);  // y = x + a y
+template <typename R>
+void vwaxpy(long long n, const R* x, R a, const R* y, R* w, cudaStream_t s);  // w = x + a y
+template <typename R>
+void vdiv(long long n, const R* x, const R* d, R* y, cudaStream_t s);  // y = x / d
+template <typename R>
+void vscal(long long n, R a, R* y, cudaStream_t s);  // y = a y
+// out[i] = <X_i, y> for i < k (X_i = X + i*ld); result in device memory (double)
+template <typename R>
+void vmdot(long long n, int k, const R* X, long long ld, const R* y, double* out, double* partial,
+           cudaStream_t s);
+// y -= sum_i coef[i] X_i   (coef in device memory, double)
+template <typename R>
+void vmaxpy(long long n, int k, const R* X, long long ld, const double* coef, double sign, R* y,
+            cudaStream_t s);
+// y = x * (1/ *nrm) with a breakdown guard (device scalar)
+template <typename R>
+void vscale_inv(long long n, const R* x, const double* nrm, R* y, cudaStream_t s);
+void dev_sqrt_store(const double* in, double* out, cudaStream_t s);
+
+}  // namespace nc

@@ -1,0 +1,626 @@
+// Solvers: Jacobi-preconditioned GMRES smoother, geometric multigrid V-cycle,
+// flexible GMRES, damped Newton with the polynomial line search (Sec. 5.1) and
+// the adjoint solve with FP64 iterative refinement (Sec. 3.2, Sec. 5.2).
+//
+// Precision: the outer FGMRES (Arnoldi with classical Gram-Schmidt applied
+// twice, Hessenberg least squares on the host), the Newton residual, the
+// refinement residual and every state update are FP64.  With mixed = 1 the
+// Jacobian products inside FGMRES, the smoother and every multigrid level run
+// in FP32; with mixed = 0 everything is FP64.
+//
+// The V-cycle and smoother run entirely on the device: their Hessenberg
+// scalars stay in device memory and a one-thread kernel solves the small
+// least-squares problem, so a preconditioner application never waits on the
+// host.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "nc_internal.cuh"
+
+namespace nc {
+nc_status set_err(nc_ctx* ctx, nc_status st, const std::string& msg);
+nc_status cuda_check(nc_ctx* ctx, cudaError_t e, const char* what);
+}  // namespace nc
+
+using namespace nc;
+
+namespace {
+
+constexpr int LDH = MAX_RESTART + 1;            // leading dimension of device Hessenbergs
+constexpr int HD_SIZE = LDH * LDH + 2 * LDH + 8;  // H, y, g, scalars
+constexpr int HD_Y = LDH * LDH;
+constexpr int HD_BETA = LDH * LDH + 2 * LDH;      // scalar slots
+constexpr int HD_TMP = HD_BETA + 1;
+
+template <typename R> LevelBuf<R>& buf(Level& L);
+template <> LevelBuf<double>& buf<double>(Level& L) { return L.f64; }
+template <> LevelBuf<float>& buf<float>(Level& L) { return L.f32; }
+template <typename R> const ElemConst<R>& cst(const Level& L);
+template <> const ElemConst<double>& cst<double>(const Level& L) { return L.c64; }
+template <> const ElemConst<float>& cst<float>(const Level& L) { return L.c32; }
+
+template <typename R>
+nc_status alloc(nc_ctx* ctx, R** p, long long n) {
+  if (*p) return NC_OK;
+  return cuda_check(ctx, cudaMalloc((void**)p, sizeof(R) * (size_t)n), "cudaMalloc");
+}
+
+// Least squares  min || beta e1 - H y ||  for a (k+1) x k upper Hessenberg H
+// (column-major, leading dimension LDH) by Givens rotations; y -> Hd[HD_Y..].
+// A vanishing pivot (exhausted Krylov space) gives the corresponding y = 0.
+__global__ void k_small_ls(double* Hd, int k) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double R[LDH * LDH];
+  double g[LDH + 1];
+  for (int j = 0; j < k; ++j)
+    for (int i = 0; i <= j + 1; ++i) R[i + j * LDH] = Hd[i + j * LDH];
+  const double beta = Hd[HD_BETA];
+  for (int i = 0; i <= k; ++i) g[i] = 0.0;
+  g[0] = (beta > 0.0 && beta < 1e300) ? beta : 0.0;
+  for (int j = 0; j < k; ++j) {
+    const double a = R[j + j * LDH], b = R[j + 1 + j * LDH];
+    const double r = hypot(a, b);
+    const double c = r > 0.0 ? a / r : 1.0, s = r > 0.0 ? b / r : 0.0;
+    for (int q = j; q < k; ++q) {
+      const double t1 = R[j + q * LDH], t2 = R[j + 1 + q * LDH];
+      R[j + q * LDH] = c * t1 + s * t2;
+      R[j + 1 + q * LDH] = -s * t1 + c * t2;
+    }
+    const double g1 = g[j], g2 = g[j + 1];
+    g[j] = c * g1 + s * g2;
+    g[j + 1] = -s * g1 + c * g2;
+  }
+  double rmax = 0.0;
+  for (int j = 0; j < k; ++j) rmax = fmax(rmax, fabs(R[j + j * LDH]));
+  for (int j = k - 1; j >= 0; --j) {
+    double acc = g[j];
+    for (int q = j + 1; q < k; ++q) acc -= R[j + q * LDH] * Hd[HD_Y + q];
+    const double d = R[j + j * LDH];
+    Hd[HD_Y + j] = (fabs(d) > 1e-14 * rmax && isfinite(acc)) ? acc / d : 0.0;
+  }
+}
+
+// ------------------------------------------------------------------ level operators
+template <typename R>
+void level_apply(nc_ctx* ctx, int l, bool tr, const R* v, R* out, cudaStream_t s) {
+  Level& L = ctx->lv[l];
+  LevelBuf<R>& B = buf<R>(L);
+  if (tr)
+    op_jtvp<R>(L.d, cst<R>(L), B.x, B.gam, B.src, v, out, (R*)ctx->Y, s);
+  else
+    op_jvp<R>(L.d, cst<R>(L), B.x, B.gam, B.src, v, out, (R*)ctx->Y, s);
+}
+
+// Right Jacobi-preconditioned GMRES(k) on level l:  z += D^-1 V y  approximately
+// solving A z = b.  With zero_init the initial guess is 0.
+template <typename R>
+void smooth(nc_ctx* ctx, int l, bool tr, int k, bool zero_init, cudaStream_t s) {
+  Level& L = ctx->lv[l];
+  LevelBuf<R>& B = buf<R>(L);
+  const long long n = 5 * L.d.Nn;
+  R* V = B.V;
+  double* Hd = B.Hd;
+  // V0 = b - A z
+  if (zero_init) {
+    vzero(n, B.z, s);
+    vcopy(n, (const R*)B.b, V, s);
+  } else {
+    level_apply<R>(ctx, l, tr, B.z, B.t, s);
+    vwaxpy(n, (const R*)B.b, R(-1), (const R*)B.t, V, s);
+  }
+  vmdot(n, 1, V, 0, V, Hd + HD_TMP, ctx->partial, s);
+  dev_sqrt_store(Hd + HD_TMP, Hd + HD_BETA, s);
+  vscale_inv(n, (const R*)V, Hd + HD_BETA, V, s);
+  for (int j = 0; j < k; ++j) {
+    R* vj = V + j * n;
+    R* w = V + (j + 1) * n;
+    vdiv(n, (const R*)vj, (const R*)B.diag, B.t, s);
+    level_apply<R>(ctx, l, tr, B.t, w, s);
+    double* hcol = Hd + j * LDH;
+    vmdot(n, j + 1, (const R*)V, n, (const R*)w, hcol, ctx->partial, s);
+    vmaxpy(n, j + 1, (const R*)V, n, hcol, 1.0, w, s);
+    vmdot(n, 1, (const R*)w, 0, (const R*)w, Hd + HD_TMP, ctx->partial, s);
+    dev_sqrt_store(Hd + HD_TMP, hcol + j + 1, s);
+    vscale_inv(n, (const R*)w, hcol + j + 1, w, s);
+  }
+  k_small_ls<<<1, 1, 0, s>>>(Hd, k);
+  // z += D^-1 (V y)
+  vzero(n, B.t, s);
+  vmaxpy(n, k, (const R*)V, n, Hd + HD_Y, -1.0, B.t, s);
+  vdiv(n, (const R*)B.t, (const R*)B.diag, B.t, s);
+  vaxpy(n, R(1), (const R*)B.t, B.z, s);
+}
+
+template <typename R>
+void vcycle(nc_ctx* ctx, int l, int nlev, bool tr, const nc_solve_opts& o, cudaStream_t s) {
+  Level& L = ctx->lv[l];
+  LevelBuf<R>& B = buf<R>(L);
+  const long long n = 5 * L.d.Nn;
+  if (l == nlev - 1) {
+    smooth<R>(ctx, l, tr, o.coarse_its, true, s);
+    return;
+  }
+  smooth<R>(ctx, l, tr, o.smooth_its, true, s);
+  level_apply<R>(ctx, l, tr, B.z, B.t, s);
+  vwaxpy(n, (const R*)B.b, R(-1), (const R*)B.t, B.r, s);
+  Level& C = ctx->lv[l + 1];
+  op_restrict<R>(L.d, B.r, C.d, buf<R>(C).b, s);
+  vcycle<R>(ctx, l + 1, nlev, tr, o, s);
+  op_prolong_add<R>(C.d, buf<R>(C).z, L.d, B.z, s);
+  smooth<R>(ctx, l, tr, o.smooth_its, false, s);
+}
+
+int n_levels(const nc_ctx* ctx, const nc_solve_opts& o) {
+  int nl = (int)ctx->lv.size();
+  if (o.mg_levels > 0 && o.mg_levels < nl) nl = o.mg_levels;
+  return nl;
+}
+
+// Allocate the per-level workspace of precision R for nlev levels.
+template <typename R>
+nc_status alloc_levels(nc_ctx* ctx, int nlev, const nc_solve_opts& o) {
+  nc_status st;
+  for (int l = 0; l < nlev; ++l) {
+    Level& L = ctx->lv[l];
+    LevelBuf<R>& B = buf<R>(L);
+    const long long n = 5 * L.d.Nn;
+    const int ks = (l == nlev - 1) ? o.coarse_its : o.smooth_its;
+    if (B.V && B.ks < ks) { cudaFree(B.V); B.V = nullptr; }
+    if ((st = alloc(ctx, &B.V, (long long)(ks + 1) * n)) != NC_OK) return st;
+    if (B.ks < ks) B.ks = ks;
+    if ((st = alloc(ctx, &B.diag, n)) != NC_OK || (st = alloc(ctx, &B.b, n)) != NC_OK ||
+        (st = alloc(ctx, &B.z, n)) != NC_OK || (st = alloc(ctx, &B.r, n)) != NC_OK ||
+        (st = alloc(ctx, &B.t, n)) != NC_OK || (st = alloc(ctx, &B.Hd, (long long)HD_SIZE)) != NC_OK)
+      return st;
+    const bool level0_f64 = (l == 0) && sizeof(R) == sizeof(double);
+    if (!level0_f64) {
+      if ((st = alloc(ctx, &B.x, n)) != NC_OK || (st = alloc(ctx, &B.gam, L.d.E)) != NC_OK)
+        return st;
+    }
+  }
+  return NC_OK;
+}
+
+// Linearisation data of every level in precision R at (x, gamma) (FP64 inputs):
+// level 0 is x, gamma themselves (FP64) or their FP32 casts; coarser levels take
+// the injected state and the mean design of the eight children; then diag(J).
+template <typename R>
+void linearize(nc_ctx* ctx, int nlev, const double* x, const double* gam, bool tr, cudaStream_t s) {
+  for (int l = 0; l < nlev; ++l) {
+    Level& L = ctx->lv[l];
+    LevelBuf<R>& B = buf<R>(L);
+    if (l == 0) {
+      if (sizeof(R) == sizeof(double)) {
+        L.f64.x = const_cast<double*>(x);
+        L.f64.gam = const_cast<double*>(gam);
+        L.f64.ext = true;
+      } else {
+        vcast(5 * L.d.Nn, x, (float*)B.x, s);
+        vcast(L.d.E, gam, (float*)B.gam, s);
+      }
+    } else {
+      Level& F = ctx->lv[l - 1];
+      op_inject<R>(F.d, buf<R>(F).x, L.d, B.x, s);
+      op_coarsen_elem<R>(F.d, buf<R>(F).gam, L.d, B.gam, s);
+    }
+    // diag(J^T) = diag(J)
+    (void)tr;
+    op_diag<R>(L.d, cst<R>(L), B.x, B.gam, B.src, B.diag, (R*)ctx->Y, s);
+  }
+}
+
+void release_ext(nc_ctx* ctx) {
+  Level& L = ctx->lv[0];
+  if (L.f64.ext) {
+    L.f64.x = nullptr;
+    L.f64.gam = nullptr;
+    L.f64.ext = false;
+  }
+}
+
+// ------------------------------------------------------------------ FGMRES (FP64)
+struct LinSolve {
+  bool tr = false;
+  bool mixed = true;
+  int nlev = 1;
+};
+
+// z = M^-1 v (one V-cycle in the chosen precision)
+void precond(nc_ctx* ctx, const LinSolve& ls, const nc_solve_opts& o, const double* v, double* z,
+             cudaStream_t s) {
+  Level& L = ctx->lv[0];
+  const long long n = 5 * L.d.Nn;
+  if (ls.mixed) {
+    vcast(n, v, L.f32.b, s);
+    vcycle<float>(ctx, 0, ls.nlev, ls.tr, o, s);
+    vcast(n, (const float*)L.f32.z, z, s);
+  } else {
+    vcopy(n, v, L.f64.b, s);
+    vcycle<double>(ctx, 0, ls.nlev, ls.tr, o, s);
+    vcopy(n, (const double*)L.f64.z, z, s);
+  }
+}
+
+// out = A v with the linear solve's operator (FP32 product in mixed mode)
+void apply_A(nc_ctx* ctx, const LinSolve& ls, const double* v, double* out, cudaStream_t s) {
+  Level& L = ctx->lv[0];
+  const long long n = 5 * L.d.Nn;
+  if (ls.mixed) {
+    vcast(n, v, L.f32.t, s);
+    level_apply<float>(ctx, 0, ls.tr, L.f32.t, L.f32.r, s);
+    vcast(n, (const float*)L.f32.r, out, s);
+  } else {
+    level_apply<double>(ctx, 0, ls.tr, v, out, s);
+  }
+}
+
+nc_status read_scalar(nc_ctx* ctx, const double* d, double* h, int k, cudaStream_t s) {
+  nc_status st = cuda_check(ctx, cudaMemcpyAsync(h, d, sizeof(double) * k, cudaMemcpyDeviceToHost, s),
+                            "read scalar");
+  if (st != NC_OK) return st;
+  return cuda_check(ctx, cudaStreamSynchronize(s), "stream sync");
+}
+
+nc_status norm2(nc_ctx* ctx, long long n, const double* v, double* out, cudaStream_t s) {
+  vmdot(n, 1, v, 0, v, ctx->dscal, ctx->partial, s);
+  double q;
+  nc_status st = read_scalar(ctx, ctx->dscal, &q, 1, s);
+  if (st != NC_OK) return st;
+  *out = std::sqrt(std::fmax(q, 0.0));
+  if (!std::isfinite(q)) return set_err(ctx, NC_ERR_NAN, "non-finite norm");
+  return NC_OK;
+}
+
+// Solve A x = b to ||b - A x|| <= rtol ||b|| (x starts at 0).  its += iterations.
+nc_status fgmres(nc_ctx* ctx, const LinSolve& ls, const nc_solve_opts& o, const double* b, double* x,
+                 double rtol, int* its, cudaStream_t s) {
+  Level& L = ctx->lv[0];
+  const long long n = 5 * L.d.Nn;
+  const int m = ctx->kry.m;
+  double* V = ctx->kry.V;
+  double* Z = ctx->kry.Z;
+  double* hc = ctx->kry.hcol;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hh(2 * (m + 2));
+  vzero(n, x, s);
+  double beta0;
+  nc_status st = norm2(ctx, n, b, &beta0, s);
+  if (st != NC_OK) return st;
+  if (beta0 == 0.0) return NC_OK;
+  bool first = true;
+  int total = 0;
+  while (total < o.max_lin) {
+    // r = b - A x  -> V0
+    if (first) {
+      vcopy(n, b, V, s);
+    } else {
+      apply_A(ctx, ls, x, ctx->kry.w, s);
+      vwaxpy(n, b, -1.0, (const double*)ctx->kry.w, V, s);
+    }
+    double beta;
+    if ((st = norm2(ctx, n, V, &beta, s)) != NC_OK) return st;
+    if (beta <= rtol * beta0) break;
+    vscal(n, 1.0 / beta, V, s);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j = 0;
+    bool done = false;
+    for (; j < m && total < o.max_lin; ++j) {
+      double* vj = V + j * n;
+      double* zj = Z + j * n;
+      double* w = V + (j + 1) * n;
+      precond(ctx, ls, o, vj, zj, s);
+      apply_A(ctx, ls, zj, w, s);
+      // classical Gram-Schmidt, twice
+      vmdot(n, j + 1, (const double*)V, n, (const double*)w, hc, ctx->partial, s);
+      vmaxpy(n, j + 1, (const double*)V, n, hc, 1.0, w, s);
+      vmdot(n, j + 1, (const double*)V, n, (const double*)w, hc + (m + 2), ctx->partial, s);
+      vmaxpy(n, j + 1, (const double*)V, n, hc + (m + 2), 1.0, w, s);
+      vmdot(n, 1, (const double*)w, 0, (const double*)w, ctx->dscal, ctx->partial, s);
+      if ((st = read_scalar(ctx, hc, hh.data(), 2 * (m + 2), s)) != NC_OK) return st;
+      double nw2;
+      if ((st = read_scalar(ctx, ctx->dscal, &nw2, 1, s)) != NC_OK) return st;
+      if (!std::isfinite(nw2)) return set_err(ctx, NC_ERR_NAN, "non-finite value in FGMRES");
+      const double nw = std::sqrt(std::fmax(nw2, 0.0));
+      for (int i = 0; i <= j; ++i) H[i + (size_t)j * (m + 1)] = hh[i] + hh[(m + 2) + i];
+      H[j + 1 + (size_t)j * (m + 1)] = nw;
+      if (nw > 0.0) vscal(n, 1.0 / nw, w, s);
+      // apply previous rotations, then a new one
+      for (int i = 0; i < j; ++i) {
+        const double t1 = H[i + (size_t)j * (m + 1)], t2 = H[i + 1 + (size_t)j * (m + 1)];
+        H[i + (size_t)j * (m + 1)] = cs[i] * t1 + sn[i] * t2;
+        H[i + 1 + (size_t)j * (m + 1)] = -sn[i] * t1 + cs[i] * t2;
+      }
+      const double a = H[j + (size_t)j * (m + 1)], bb = H[j + 1 + (size_t)j * (m + 1)];
+      const double r = std::hypot(a, bb);
+      cs[j] = r > 0.0 ? a / r : 1.0;
+      sn[j] = r > 0.0 ? bb / r : 0.0;
+      H[j + (size_t)j * (m + 1)] = r;
+      H[j + 1 + (size_t)j * (m + 1)] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++total;
+      if (std::fabs(g[j + 1]) <= rtol * beta0 || nw == 0.0) {
+        ++j;
+        done = true;
+        break;
+      }
+    }
+    // y = H^-1 g, x += Z y
+    std::vector<double> y(j);
+    for (int i = j - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int q = i + 1; q < j; ++q) acc -= H[i + (size_t)q * (m + 1)] * y[q];
+      const double d = H[i + (size_t)i * (m + 1)];
+      y[i] = d != 0.0 ? acc / d : 0.0;
+    }
+    if (j > 0) {
+      if ((st = cuda_check(ctx, cudaMemcpyAsync(ctx->kry.y, y.data(), sizeof(double) * j,
+                                                cudaMemcpyHostToDevice, s), "upload y")) != NC_OK)
+        return st;
+      vmaxpy(n, j, (const double*)Z, n, ctx->kry.y, -1.0, x, s);
+      if ((st = cuda_check(ctx, cudaStreamSynchronize(s), "fgmres sync")) != NC_OK) return st;
+    }
+    first = false;
+    if (done) break;
+  }
+  *its += total;
+  if (total >= o.max_lin) {
+    // final check of the true residual
+    apply_A(ctx, ls, x, ctx->kry.w, s);
+    vwaxpy(n, b, -1.0, (const double*)ctx->kry.w, V, s);
+    double rn;
+    if ((st = norm2(ctx, n, V, &rn, s)) != NC_OK) return st;
+    if (rn > rtol * beta0) return set_err(ctx, NC_ERR_MAXIT, "FGMRES reached max_lin");
+  }
+  return NC_OK;
+}
+
+nc_status prepare(nc_ctx* ctx, const nc_solve_opts& o, int nlev, bool mixed) {
+  Level& L = ctx->lv[0];
+  const long long n = 5 * L.d.Nn;
+  nc_status st;
+  if (o.restart < 1 || o.restart > MAX_RESTART || o.smooth_its < 1 ||
+      o.smooth_its > MAX_RESTART || o.coarse_its < 1 || o.coarse_its > MAX_RESTART ||
+      o.max_lin < 1 || o.max_newton < 0 || !(o.rtol_lin > 0.0) || !(o.rtol_newton >= 0.0))
+    return set_err(ctx, NC_ERR_ARG, "invalid solver options");
+  if (ctx->kry.m < o.restart) {
+    cudaFree(ctx->kry.V);
+    cudaFree(ctx->kry.Z);
+    ctx->kry.V = ctx->kry.Z = nullptr;
+    ctx->kry.m = 0;
+  }
+  if (!ctx->kry.V) {
+    if ((st = alloc(ctx, &ctx->kry.V, (long long)(o.restart + 1) * n)) != NC_OK ||
+        (st = alloc(ctx, &ctx->kry.Z, (long long)o.restart * n)) != NC_OK)
+      return st;
+    ctx->kry.m = o.restart;
+  }
+  if ((st = alloc(ctx, &ctx->kry.w, n)) != NC_OK ||
+      (st = alloc(ctx, &ctx->kry.hcol, 2LL * (MAX_RESTART + 2))) != NC_OK ||
+      (st = alloc(ctx, &ctx->kry.y, (long long)MAX_RESTART)) != NC_OK)
+    return st;
+  for (int i = 0; i < 6; ++i)
+    if ((st = alloc(ctx, &ctx->tmp64[i], n)) != NC_OK) return st;
+  if (mixed) {
+    if ((st = alloc_levels<float>(ctx, nlev, o)) != NC_OK) return st;
+  } else {
+    if ((st = alloc_levels<double>(ctx, nlev, o)) != NC_OK) return st;
+  }
+  return NC_OK;
+}
+
+void set_Gr(nc_ctx* ctx, double Gr) {
+  const nc_params& p = ctx->prm;
+  for (auto& L : ctx->lv) {
+    L.c64 = make_const<double>(L.d.h, Gr, p.Pr, p.alpha_max, p.q_alpha, p.q_f, p.Ck, p.g_dir);
+    L.c32 = make_const<float>(L.d.h, Gr, p.Pr, p.alpha_max, p.q_alpha, p.q_f, p.Ck, p.g_dir);
+  }
+}
+
+double line_search_length(double n0, double nh, double n1) {
+  const double a = 2.0 * (n1 - 2.0 * nh + n0);
+  const double b = n1 - n0 - a;
+  if (a > 0.0) {
+    const double lam = -b / (2.0 * a);
+    if (lam > 0.0 && lam <= 1.0) return std::fmax(lam, 0.05);
+  }
+  return nh < n1 ? 0.5 : 1.0;
+}
+
+// Newton at the context's current Gr, from x (Dirichlet values already imposed).
+nc_status newton(nc_ctx* ctx, const double* gam, double* x, const nc_solve_opts& o,
+                 nc_solve_info* info, cudaStream_t s) {
+  Level& L = ctx->lv[0];
+  const long long n = 5 * L.d.Nn;
+  const int nlev = n_levels(ctx, o);
+  const bool mixed = o.mixed != 0;
+  double* R = ctx->tmp64[0];
+  double* d = ctx->tmp64[1];
+  double* xt = ctx->tmp64[2];
+  double* Rh = ctx->tmp64[3];
+  double* R1 = ctx->tmp64[4];
+  nc_status st;
+  op_residual<double>(L.d, L.c64, x, gam, ctx->src64, R, ctx->Y, s);
+  double nr;
+  if ((st = norm2(ctx, n, R, &nr, s)) != NC_OK) return st;
+  const double r0 = nr;
+  if (info->newton_its == 0 && info->res0 == 0.0) info->res0 = r0;
+  int it = 0;
+  auto hist = [&](double v) {
+    const int k = info->newton_its;
+    if (k < 64) info->res_hist[k] = v;
+  };
+  if (info->newton_its == 0) hist(r0);
+  const LinSolve ls{false, mixed, nlev};
+  while (nr > o.rtol_newton * r0 && nr > 0.0) {
+    if (it >= o.max_newton) {
+      info->res_final = nr;
+      return set_err(ctx, NC_ERR_MAXIT, "Newton reached max_newton");
+    }
+    if (mixed) linearize<float>(ctx, nlev, x, gam, false, s);
+    else linearize<double>(ctx, nlev, x, gam, false, s);
+    // J d = R, the Newton step is -d
+    int lits = 0;
+    st = fgmres(ctx, ls, o, R, d, o.rtol_lin, &lits, s);
+    release_ext(ctx);
+    info->lin_its_total += lits;
+    if (st != NC_OK && st != NC_ERR_MAXIT) return st;
+    vwaxpy(n, (const double*)x, -0.5, (const double*)d, xt, s);
+    op_residual<double>(L.d, L.c64, xt, gam, ctx->src64, Rh, ctx->Y, s);
+    double nh, n1;
+    if ((st = norm2(ctx, n, Rh, &nh, s)) != NC_OK) return st;
+    vwaxpy(n, (const double*)x, -1.0, (const double*)d, xt, s);
+    op_residual<double>(L.d, L.c64, xt, gam, ctx->src64, R1, ctx->Y, s);
+    if ((st = norm2(ctx, n, R1, &n1, s)) != NC_OK) return st;
+    const double lam = line_search_length(nr, nh, n1);
+    double nn;
+    if (lam == 1.0) {
+      vcopy(n, (const double*)xt, x, s);
+      vcopy(n, (const double*)R1, R, s);
+      nn = n1;
+    } else if (lam == 0.5) {
+      vaxpy(n, -0.5, (const double*)d, x, s);
+      vcopy(n, (const double*)Rh, R, s);
+      nn = nh;
+    } else {
+      vaxpy(n, -lam, (const double*)d, x, s);
+      op_residual<double>(L.d, L.c64, x, gam, ctx->src64, R, ctx->Y, s);
+      if ((st = norm2(ctx, n, R, &nn, s)) != NC_OK) return st;
+    }
+    ++it;
+    ++info->newton_its;
+    hist(nn);
+    if (!(nn < nr) && !(std::fmin(nh, n1) < nr)) {
+      nr = nn;
+      info->res_final = nr;
+      return set_err(ctx, NC_ERR_DIVERGED, "Newton: no decrease of the residual norm");
+    }
+    nr = nn;
+  }
+  info->res_final = nr;
+  return NC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void nc_default_opts(nc_solve_opts* o) {
+  if (!o) return;
+  o->rtol_newton = 1e-8;
+  o->rtol_lin = 1e-5;
+  o->max_newton = 30;
+  o->max_lin = 200;
+  o->restart = 30;
+  o->mg_levels = 0;
+  o->smooth_its = 2;
+  o->coarse_its = 30;
+  o->mixed = 1;
+  o->ramp_steps = 0;
+}
+
+nc_status nc_newton_solve(nc_ctx* ctx, const double* gam, double* x, const nc_solve_opts* opts,
+                          nc_solve_info* info_out, void* stream) {
+  if (!ctx || !gam || !x) return set_err(ctx, NC_ERR_ARG, "nc_newton_solve: NULL argument");
+  nc_solve_opts o;
+  nc_default_opts(&o);
+  if (opts) o = *opts;
+  cudaStream_t s = (cudaStream_t)stream;
+  nc_solve_info info;
+  std::memset(&info, 0, sizeof(info));
+  const auto t0 = std::chrono::steady_clock::now();
+  const int nlev = n_levels(ctx, o);
+  nc_status st = prepare(ctx, o, nlev, o.mixed != 0);
+  if (st == NC_OK) {
+    Level& L = ctx->lv[0];
+    const long long n = 5 * L.d.Nn;
+    op_impose<double>(L.d, x, s);
+    // keep the start for a ramped retry
+    if (o.ramp_steps > 0) vcopy(n, (const double*)x, ctx->tmp64[5], s);
+    st = newton(ctx, gam, x, o, &info, s);
+    if (st != NC_OK && st != NC_ERR_ARG && st != NC_ERR_CUDA && st != NC_ERR_OOM &&
+        o.ramp_steps > 0) {
+      // ramp the buoyancy: Gr / 10^steps, ..., Gr / 10, Gr, each from the last state
+      vcopy(n, (const double*)ctx->tmp64[5], x, s);
+      info.res0 = 0.0;
+      info.newton_its = 0;
+      for (int k = o.ramp_steps; k >= 0; --k) {
+        set_Gr(ctx, ctx->prm.Gr * std::pow(10.0, -k));
+        st = newton(ctx, gam, x, o, &info, s);
+        if (st != NC_OK && k == 0) break;
+        if (st != NC_OK && st != NC_ERR_MAXIT && st != NC_ERR_DIVERGED) break;
+      }
+      set_Gr(ctx, ctx->prm.Gr);
+    }
+  }
+  release_ext(ctx);
+  const nc_status st2 = cuda_check(ctx, cudaStreamSynchronize(s), "nc_newton_solve");
+  if (st == NC_OK) st = st2;
+  info.status = st;
+  info.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info_out) *info_out = info;
+  return st;
+}
+
+nc_status nc_adjoint_solve(nc_ctx* ctx, const double* x, const double* gam, const double* rhs,
+                           double* lam, const nc_solve_opts* opts, nc_solve_info* info_out,
+                           void* stream) {
+  if (!ctx || !x || !gam || !rhs || !lam) return set_err(ctx, NC_ERR_ARG, "nc_adjoint_solve: NULL argument");
+  nc_solve_opts o;
+  nc_default_opts(&o);
+  if (opts) o = *opts;
+  cudaStream_t s = (cudaStream_t)stream;
+  nc_solve_info info;
+  std::memset(&info, 0, sizeof(info));
+  const auto t0 = std::chrono::steady_clock::now();
+  const int nlev = n_levels(ctx, o);
+  const bool mixed = o.mixed != 0;
+  nc_status st = prepare(ctx, o, nlev, mixed);
+  if (st == NC_OK) {
+    Level& L = ctx->lv[0];
+    const long long n = 5 * L.d.Nn;
+    double* r = ctx->tmp64[0];
+    double* dl = ctx->tmp64[1];
+    double* t = ctx->tmp64[2];
+    vzero(n, lam, s);
+    vcopy(n, rhs, r, s);
+    double nb;
+    st = norm2(ctx, n, rhs, &nb, s);
+    info.res0 = nb;
+    info.res_hist[0] = nb;
+    const LinSolve ls{true, mixed, nlev};
+    int k = 0;
+    double nr = nb;
+    while (st == NC_OK && nr > o.rtol_newton * nb && nr > 0.0) {
+      if (k >= o.max_newton) { st = set_err(ctx, NC_ERR_MAXIT, "adjoint refinement limit"); break; }
+      if (mixed) linearize<float>(ctx, nlev, x, gam, true, s);
+      else linearize<double>(ctx, nlev, x, gam, true, s);
+      int lits = 0;
+      // inner relative tolerance: no tighter than needed for the outer target
+      const double rt = std::fmax(o.rtol_lin, 0.5 * o.rtol_newton * nb / nr);
+      st = fgmres(ctx, ls, o, r, dl, std::fmin(rt, 0.5), &lits, s);
+      release_ext(ctx);
+      info.lin_its_total += lits;
+      if (st != NC_OK && st != NC_ERR_MAXIT) break;
+      vaxpy(n, 1.0, (const double*)dl, lam, s);
+      // FP64 refinement residual r = rhs - J^T lam
+      op_jtvp<double>(L.d, L.c64, x, gam, ctx->src64, lam, t, ctx->Y, s);
+      vwaxpy(n, rhs, -1.0, (const double*)t, r, s);
+      if ((st = norm2(ctx, n, r, &nr, s)) != NC_OK) break;
+      ++k;
+      if (k < 64) info.res_hist[k] = nr;
+    }
+    info.newton_its = k;
+    info.res_final = nr;
+  }
+  release_ext(ctx);
+  const nc_status st2 = cuda_check(ctx, cudaStreamSynchronize(s), "nc_adjoint_solve");
+  if (st == NC_OK) st = st2;
+  info.status = st;
+  info.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info_out) *info_out = info;
+  return st;
+}
+
+}  // extern "C"

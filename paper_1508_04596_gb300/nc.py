@@ -1,0 +1,303 @@
+"""Python binding of libnc (argument marshalling only).
+
+Every operation runs in the CUDA library ``libnc.so`` built from ``csrc/``; this
+module checks tensor dtypes, devices and shapes, passes raw device pointers and
+the current CUDA stream through the C ABI declared in ``include/nc.h``, and
+turns status codes into exceptions.  There is no CPU fallback: importing this
+module fails if the library has not been built.
+"""
+import ctypes
+import os
+
+import torch
+
+from . import synth
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnc.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libnc.so is not built (run __graft_entry__.build() or "
+                      "python -m paper_1508_04596_gb300.build); no CPU fallback exists")
+lib = ctypes.CDLL(LIB_PATH)
+
+NC_FP64, NC_FP32 = 0, 1
+VEL_NOSLIP, VEL_FREE, VEL_SYMMETRY = 0, 1, 2
+T_ADIABATIC, T_DIRICHLET = 0, 1
+PATCH_NONE, PATCH_DIRICHLET, PATCH_FLUX = 0, 1, 2
+STATUS = {0: "NC_OK", 1: "NC_ERR_ARG", 2: "NC_ERR_CUDA", 3: "NC_ERR_OOM", 4: "NC_ERR_NAN",
+          5: "NC_ERR_MAXIT", 6: "NC_ERR_DIVERGED"}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("h", ctypes.c_double), ("Gr", ctypes.c_double), ("Pr", ctypes.c_double),
+                ("alpha_max", ctypes.c_double), ("q_alpha", ctypes.c_double),
+                ("q_f", ctypes.c_double), ("Ck", ctypes.c_double),
+                ("g_dir", ctypes.c_double * 3)]
+
+
+class BCs(ctypes.Structure):
+    _fields_ = [("vel_bc", ctypes.c_int * 6), ("T_bc", ctypes.c_int * 6),
+                ("T_val", ctypes.c_double * 6), ("patch", ctypes.c_double * 4),
+                ("patch_mode", ctypes.c_int), ("patch_val", ctypes.c_double),
+                ("p_pin", ctypes.c_longlong)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("rtol_newton", ctypes.c_double), ("rtol_lin", ctypes.c_double),
+                ("max_newton", ctypes.c_int), ("max_lin", ctypes.c_int),
+                ("restart", ctypes.c_int), ("mg_levels", ctypes.c_int),
+                ("smooth_its", ctypes.c_int), ("coarse_its", ctypes.c_int),
+                ("mixed", ctypes.c_int), ("ramp_steps", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("newton_its", ctypes.c_int), ("lin_its_total", ctypes.c_int),
+                ("status", ctypes.c_int), ("res0", ctypes.c_double),
+                ("res_final", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("res_hist", ctypes.c_double * 64)]
+
+    def as_dict(self):
+        k = min(self.newton_its + 1, 64)
+        return dict(newton_its=self.newton_its, lin_its_total=self.lin_its_total,
+                    status=STATUS.get(self.status, self.status), res0=self.res0,
+                    res_final=self.res_final, seconds=self.seconds,
+                    res_hist=list(self.res_hist[:k]))
+
+
+_vp = ctypes.c_void_p
+_ctx = ctypes.c_void_p
+_SIGS = {
+    "nc_sizes": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_longlong),
+                                ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+    "nc_setup": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(BCs), ctypes.POINTER(_ctx)]),
+    "nc_destroy": (None, [_ctx]),
+    "nc_last_error": (ctypes.c_char_p, [_ctx]),
+    "nc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "nc_bc_flags": (ctypes.c_int, [_ctx, _vp]),
+    "nc_set_source": (ctypes.c_int, [_ctx, _vp, _vp]),
+    "nc_impose_dirichlet": (ctypes.c_int, [_ctx, _vp, ctypes.c_int, _vp]),
+    "nc_residual": (ctypes.c_int, [_ctx, _vp, _vp, _vp, ctypes.c_int, _vp]),
+    "nc_jvp": (ctypes.c_int, [_ctx, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
+    "nc_jtvp": (ctypes.c_int, [_ctx, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
+    "nc_diag": (ctypes.c_int, [_ctx, _vp, _vp, _vp, ctypes.c_int, _vp]),
+    "nc_objective": (ctypes.c_int, [_ctx, _vp, ctypes.POINTER(ctypes.c_double), _vp, _vp]),
+    "nc_sensitivity": (ctypes.c_int, [_ctx, _vp, _vp, _vp, _vp, _vp]),
+    "nc_default_opts": (None, [ctypes.POINTER(SolveOpts)]),
+    "nc_newton_solve": (ctypes.c_int, [_ctx, _vp, _vp, ctypes.POINTER(SolveOpts),
+                                       ctypes.POINTER(SolveInfo), _vp]),
+    "nc_adjoint_solve": (ctypes.c_int, [_ctx, _vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts),
+                                        ctypes.POINTER(SolveInfo), _vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class NCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+def default_opts(**kw):
+    o = SolveOpts()
+    lib.nc_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def cavity_bcs(patch_mode=PATCH_DIRICHLET, patch_val=1.0, patch=(1 / 3, 2 / 3, 1 / 3, 2 / 3)):
+    """Heated-base cavity: no-slip walls and bottom, traction-free top at T = 0,
+    side walls at T = 0, bottom adiabatic outside a central patch that is held
+    at T = patch_val or heated by the inward flux patch_val."""
+    b = BCs()
+    b.vel_bc[:] = [VEL_NOSLIP] * 5 + [VEL_FREE]
+    b.T_bc[:] = [T_DIRICHLET] * 4 + [T_ADIABATIC, T_DIRICHLET]
+    b.T_val[:] = [0.0] * 6
+    b.patch[:] = list(patch)
+    b.patch_mode = patch_mode
+    b.patch_val = patch_val
+    b.p_pin = -1
+    return b
+
+
+def make_params(nx, ny, nz, h, Gr, Pr, alpha_max=1e4, q_alpha=1.0, q_f=1.0, Ck=0.1,
+                g_dir=(0.0, 0.0, -1.0)):
+    p = Params()
+    p.nx, p.ny, p.nz, p.h = nx, ny, nz, h
+    p.Gr, p.Pr = Gr, Pr
+    p.alpha_max, p.q_alpha, p.q_f, p.Ck = alpha_max, q_alpha, q_f, Ck
+    p.g_dir[:] = list(g_dir)
+    return p
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
+
+
+class Problem:
+    """A discrete problem on the current CUDA device (owns an nc_ctx)."""
+
+    def __init__(self, params, bcs):
+        self.params, self.bcs = params, bcs
+        ctx = _ctx()
+        st = lib.nc_setup(ctypes.byref(params), ctypes.byref(bcs), ctypes.byref(ctx))
+        if st != 0:
+            raise NCError(st, "nc_setup failed")
+        self.ctx = ctx
+        nn, ne, nd = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        lib.nc_sizes(ctypes.byref(params), ctypes.byref(nn), ctypes.byref(ne), ctypes.byref(nd))
+        self.Nn, self.E, self.ndof = nn.value, ne.value, nd.value
+
+    @classmethod
+    def from_workload(cls, name, **over):
+        cfg = dict(synth.WORKLOADS[name])
+        cfg.update(over)
+        mat = dict(synth.MATERIAL)
+        mat.update({k: over[k] for k in ("alpha_max", "q_alpha", "q_f", "Ck") if k in over})
+        p = make_params(cfg["nx"], cfg["ny"], cfg["nz"], cfg["h"], cfg["Gr"], cfg["Pr"], **mat)
+        mode = PATCH_FLUX if cfg["patch"] == "flux" else PATCH_DIRICHLET
+        return cls(p, cavity_bcs(mode, 1.0))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib.nc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, st):
+        if st != 0:
+            raise NCError(st, lib.nc_last_error(self.ctx).decode())
+
+    def _vec(self, t, dtype, n, name):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype
+                and t.is_contiguous() and t.numel() == n):
+            raise ValueError("%s must be a contiguous CUDA %s tensor with %d elements" % (name, dtype, n))
+        return ctypes.c_void_p(t.data_ptr())
+
+    @staticmethod
+    def _prec(x):
+        return NC_FP64 if x.dtype == torch.float64 else NC_FP32
+
+    # ---- operators -------------------------------------------------------
+    def residual(self, x, gam, out=None, stream=None):
+        out = torch.empty_like(x) if out is None else out
+        dt = x.dtype
+        self._chk(lib.nc_residual(self.ctx, self._vec(x, dt, self.ndof, "x"),
+                                  self._vec(gam, dt, self.E, "gamma"),
+                                  self._vec(out, dt, self.ndof, "r"), self._prec(x), _stream(stream)))
+        return out
+
+    def jvp(self, x, gam, v, out=None, stream=None):
+        out = torch.empty_like(x) if out is None else out
+        dt = x.dtype
+        self._chk(lib.nc_jvp(self.ctx, self._vec(x, dt, self.ndof, "x"),
+                             self._vec(gam, dt, self.E, "gamma"), self._vec(v, dt, self.ndof, "v"),
+                             self._vec(out, dt, self.ndof, "Jv"), self._prec(x), _stream(stream)))
+        return out
+
+    def jtvp(self, x, gam, w, out=None, stream=None):
+        out = torch.empty_like(x) if out is None else out
+        dt = x.dtype
+        self._chk(lib.nc_jtvp(self.ctx, self._vec(x, dt, self.ndof, "x"),
+                              self._vec(gam, dt, self.E, "gamma"), self._vec(w, dt, self.ndof, "w"),
+                              self._vec(out, dt, self.ndof, "JTw"), self._prec(x), _stream(stream)))
+        return out
+
+    def diag(self, x, gam, out=None, stream=None):
+        out = torch.empty_like(x) if out is None else out
+        dt = x.dtype
+        self._chk(lib.nc_diag(self.ctx, self._vec(x, dt, self.ndof, "x"),
+                              self._vec(gam, dt, self.E, "gamma"),
+                              self._vec(out, dt, self.ndof, "d"), self._prec(x), _stream(stream)))
+        return out
+
+    def impose_dirichlet(self, x, stream=None):
+        self._chk(lib.nc_impose_dirichlet(self.ctx, self._vec(x, x.dtype, self.ndof, "x"),
+                                          self._prec(x), _stream(stream)))
+        return x
+
+    def bc_flags(self):
+        import numpy as np
+        out = np.zeros(self.Nn, dtype=np.uint8)
+        self._chk(lib.nc_bc_flags(self.ctx, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def set_source(self, s_e, stream=None):
+        p = None if s_e is None else self._vec(s_e, torch.float64, self.E, "source")
+        self._chk(lib.nc_set_source(self.ctx, p, _stream(stream)))
+
+    def objective(self, x, want_grad=True, stream=None):
+        phi = ctypes.c_double()
+        g = torch.empty_like(x) if want_grad else None
+        self._chk(lib.nc_objective(self.ctx, self._vec(x, torch.float64, self.ndof, "x"),
+                                   ctypes.byref(phi),
+                                   None if g is None else ctypes.c_void_p(g.data_ptr()),
+                                   _stream(stream)))
+        return phi.value, g
+
+    def sensitivity(self, x, gam, lam, out=None, stream=None):
+        out = torch.empty_like(gam) if out is None else out
+        self._chk(lib.nc_sensitivity(self.ctx, self._vec(x, torch.float64, self.ndof, "x"),
+                                     self._vec(gam, torch.float64, self.E, "gamma"),
+                                     self._vec(lam, torch.float64, self.ndof, "lambda"),
+                                     self._vec(out, torch.float64, self.E, "dphidgamma"),
+                                     _stream(stream)))
+        return out
+
+    # ---- solvers ---------------------------------------------------------
+    def newton_solve(self, gam, x, opts=None, stream=None, check=True):
+        opts = default_opts() if opts is None else opts
+        info = SolveInfo()
+        st = lib.nc_newton_solve(self.ctx, self._vec(gam, torch.float64, self.E, "gamma"),
+                                 self._vec(x, torch.float64, self.ndof, "x"), ctypes.byref(opts),
+                                 ctypes.byref(info), _stream(stream))
+        if check:
+            self._chk(st)
+        return x, info.as_dict()
+
+    def adjoint_solve(self, x, gam, rhs, lam=None, opts=None, stream=None, check=True):
+        opts = default_opts() if opts is None else opts
+        lam = torch.empty_like(x) if lam is None else lam
+        info = SolveInfo()
+        st = lib.nc_adjoint_solve(self.ctx, self._vec(x, torch.float64, self.ndof, "x"),
+                                  self._vec(gam, torch.float64, self.E, "gamma"),
+                                  self._vec(rhs, torch.float64, self.ndof, "rhs"),
+                                  self._vec(lam, torch.float64, self.ndof, "lambda"),
+                                  ctypes.byref(opts), ctypes.byref(info), _stream(stream))
+        if check:
+            self._chk(st)
+        return lam, info.as_dict()
+
+
+class PatchTemperature(torch.autograd.Function):
+    """Phi(gamma) = mean patch temperature of the converged state (forward:
+    Newton solve + objective); backward: adjoint solve J^T lambda = -dPhi/dx and
+    the element sensitivities lambda^T dR/dgamma (Sec. 3.2, App. B)."""
+
+    @staticmethod
+    def forward(ctx, gam, prob, x0, opts):
+        x = x0.detach().clone()
+        prob.newton_solve(gam.detach(), x, opts)
+        phi, dphi = prob.objective(x)
+        ctx.prob, ctx.opts = prob, opts
+        ctx.save_for_backward(gam.detach(), x, dphi)
+        return torch.tensor(phi, dtype=torch.float64, device=gam.device)
+
+    @staticmethod
+    def backward(ctx, grad):
+        gam, x, dphi = ctx.saved_tensors
+        lam, _ = ctx.prob.adjoint_solve(x, gam, -dphi, opts=ctx.opts)
+        sens = ctx.prob.sensitivity(x, gam, lam)
+        return grad * sens, None, None, None

@@ -1,0 +1,232 @@
+"""GPU parity: libnc (through its C ABI) against the FP64 oracle on the same
+seeded inputs.
+
+Tolerances.  FP64: relative L2 <= 1e-12 for the residual, J v, J^T w, diag(J)
+and the element sensitivities (random BC-consistent states, ||R|| = O(1)).
+Integer work (boundary flags) is compared bit for bit.  FP32: the kernels round
+every input to FP32 (relative 6e-8) and accumulate about 10^3 terms per output
+in FP32, with cancellation between the pressure gradient and the buoyancy term
+of up to two orders of magnitude; the bound used is relative L2 <= 2e-4.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import grid as G  # noqa: E402
+from oracle import solve as S  # noqa: E402
+from paper_1508_04596_gb300 import synth  # noqa: E402
+from tests.helpers import oracle_problem, random_bc_state, sampled_rows  # noqa: E402
+
+TOL64 = 1e-12
+TOL32 = 2e-4
+
+
+@pytest.fixture(scope="module")
+def nc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1508_04596_gb300 import nc as ncmod
+    return ncmod
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def dev(a, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a).ravel(), dtype=dtype, device="cuda")
+
+
+def host(t, shape=None):
+    a = t.detach().double().cpu().numpy()
+    return a if shape is None else a.reshape(shape)
+
+
+# grids: cfg-0 cube, ragged non-cubic, flux patch
+CASES = [
+    dict(nx=12, ny=12, nz=12, Gr=1e3, patch="dirichlet", seed=0),
+    dict(nx=5, ny=7, nz=6, Gr=1e4, patch="flux", seed=1),
+    dict(nx=9, ny=4, nz=3, Gr=1e5, patch="dirichlet", seed=2),
+]
+
+
+def make_pair(nc, c):
+    h = 1.0 / c["nx"]
+    prob, bc = oracle_problem(c["nx"], c["ny"], c["nz"], h, c["Gr"], 0.71, patch_mode=c["patch"])
+    p = nc.make_params(c["nx"], c["ny"], c["nz"], h, c["Gr"], 0.71, **synth.MATERIAL)
+    mode = nc.PATCH_FLUX if c["patch"] == "flux" else nc.PATCH_DIRICHLET
+    gp = nc.Problem(p, nc.cavity_bcs(mode, 1.0))
+    gam = synth.smoothed_random(c["nx"], c["ny"], c["nz"], h, c["seed"])
+    x = random_bc_state(prob, 100 + c["seed"])
+    return prob, bc, gp, gam, x
+
+
+@pytest.mark.parametrize("c", CASES)
+def test_bc_flags_bit_exact(nc, c):
+    prob, bc, gp, gam, x = make_pair(nc, c)
+    fl = gp.bc_flags()
+    mask = np.zeros((5, prob.g.Nn), bool)
+    for f in range(5):
+        mask[f] = (fl >> f) & 1
+    assert np.array_equal(mask, prob.dmask)
+
+
+def test_bc_flags_symmetry_and_pin(nc):
+    bc = G.BCs(vel_bc=(G.SYMMETRY, G.NOSLIP, G.NOSLIP, G.SYMMETRY, G.NOSLIP, G.NOSLIP),
+               patch_mode=G.PATCH_FLUX, p_pin=7)
+    prob, _ = oracle_problem(4, 6, 5, 0.25, 1e3, 0.71, bc=bc)
+    b = nc.BCs()
+    b.vel_bc[:] = [2, 0, 0, 2, 0, 0]
+    b.T_bc[:] = [1, 1, 1, 1, 0, 1]
+    b.T_val[:] = [0.0] * 6
+    b.patch[:] = [1 / 3, 2 / 3, 1 / 3, 2 / 3]
+    b.patch_mode, b.patch_val, b.p_pin = 2, 1.0, 7
+    gp = nc.Problem(nc.make_params(4, 6, 5, 0.25, 1e3, 0.71), b)
+    fl = gp.bc_flags()
+    for f in range(5):
+        assert np.array_equal(((fl >> f) & 1).astype(bool), prob.dmask[f])
+
+
+@pytest.mark.parametrize("c", CASES)
+def test_residual_fp64(nc, c):
+    prob, bc, gp, gam, x = make_pair(nc, c)
+    R = gp.residual(dev(x), dev(gam))
+    Ro = prob.residual(x, gam)
+    assert np.linalg.norm(Ro) > 1e-3
+    assert rel(host(R, Ro.shape), Ro) <= TOL64
+
+
+@pytest.mark.parametrize("c", CASES)
+def test_jvp_jtvp_diag_fp64(nc, c):
+    prob, bc, gp, gam, x = make_pair(nc, c)
+    J = prob.jacobian(x, gam)
+    xd, gd = dev(x), dev(gam)
+    rng = np.random.default_rng(c["seed"] + 7)
+    for s in range(16 if c["nx"] == 12 else 4):
+        v = rng.standard_normal(prob.g.ndof)
+        Jv = gp.jvp(xd, gd, dev(v))
+        assert rel(host(Jv), J @ v) <= TOL64
+        JTw = gp.jtvp(xd, gd, dev(v))
+        assert rel(host(JTw), J.T @ v) <= TOL64
+    d = gp.diag(xd, gd)
+    assert rel(host(d), J.diagonal()) <= TOL64
+
+
+@pytest.mark.parametrize("c", CASES)
+def test_fp32_operators(nc, c):
+    prob, bc, gp, gam, x = make_pair(nc, c)
+    J = prob.jacobian(x, gam)
+    f = torch.float32
+    xd, gd = dev(x, f), dev(gam, f)
+    v = np.random.default_rng(3).standard_normal(prob.g.ndof)
+    assert rel(host(gp.residual(xd, gd), (5, -1)), prob.residual(x, gam)) <= TOL32
+    assert rel(host(gp.jvp(xd, gd, dev(v, f))), J @ v) <= TOL32
+    assert rel(host(gp.jtvp(xd, gd, dev(v, f))), J.T @ v) <= TOL32
+    assert rel(host(gp.diag(xd, gd)), J.diagonal()) <= TOL32
+
+
+@pytest.mark.parametrize("c", CASES)
+def test_sensitivity_and_objective(nc, c):
+    prob, bc, gp, gam, x = make_pair(nc, c)
+    lam = np.random.default_rng(5).standard_normal((5, prob.g.Nn))
+    s_gpu = host(gp.sensitivity(dev(x), dev(gam), dev(lam)))
+    s_or = S.sensitivity(prob, x, gam, lam)
+    assert rel(s_gpu, s_or) <= TOL64
+    phi, g = gp.objective(dev(x))
+    phi_o, g_o = S.objective(prob, bc, x)
+    assert phi == pytest.approx(phi_o, rel=1e-13, abs=1e-15)
+    assert np.array_equal(host(g, g_o.shape) != 0, g_o != 0)
+    assert rel(host(g, g_o.shape), g_o) <= 1e-15
+
+
+def test_adjoint_dot_product_32cube(nc):
+    """w^T (J v) = (J^T w)^T v at a size beyond the oracle's (32^3, FP64)."""
+    n = 32
+    p = nc.make_params(n, n, n, 1.0 / n, 1e5, 0.71, **synth.MATERIAL)
+    gp = nc.Problem(p, nc.cavity_bcs())
+    rng = np.random.default_rng(11)
+    gam = dev(synth.smoothed_random(n, n, n, 1.0 / n, 4))
+    x = dev(synth.random_state(n, n, n, 12, (0.5, 0.5, 0.5, 50, 1)))
+    gp.impose_dirichlet(x)
+    v, w = dev(rng.standard_normal(gp.ndof)), dev(rng.standard_normal(gp.ndof))
+    a = torch.dot(w, gp.jvp(x, gam, v)).item()
+    b = torch.dot(gp.jtvp(x, gam, w), v).item()
+    assert a == pytest.approx(b, rel=1e-12)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_fins64_sampled_rows(nc, prec):
+    """64^3 fins workload in the launch configuration the benchmark times: J v
+    and J^T w rows at 48 sampled nodes against element-by-element oracle rows."""
+    name = "fins64_gr1e4"
+    cfg = synth.WORKLOADS[name]
+    gp = nc.Problem.from_workload(name)
+    n = cfg["nx"]
+    prob, bc = oracle_problem(n, n, n, cfg["h"], cfg["Gr"], cfg["Pr"])
+    gam = synth.design(name)
+    x = random_bc_state(prob, 21)
+    rng = np.random.default_rng(22)
+    v = rng.standard_normal((5, prob.g.Nn))
+    dt = torch.float64 if prec == "f64" else torch.float32
+    tol = TOL64 * 10 if prec == "f64" else TOL32
+    Jv = host(gp.jvp(dev(x, dt), dev(gam, dt), dev(v, dt)), (5, -1))
+    JTw = host(gp.jtvp(dev(x, dt), dev(gam, dt), dev(v, dt)), (5, -1))
+    nodes = rng.choice(prob.g.Nn, size=48, replace=False)
+    vm = np.where(prob.dmask, 0.0, v)
+    for kind, got in (("jvp", Jv), ("jtvp", JTw)):
+        ref = sampled_rows(prob.g, prob.prm, x, gam, vm, nodes, kind)
+        ref = np.where(prob.dmask[:, nodes], v[:, nodes], ref)
+        assert rel(got[:, nodes], ref) <= tol, kind
+
+
+def test_newton_matches_oracle_cfg0(nc):
+    """cavity12_gr1e3: Newton-FGMRES-multigrid (FP64 and mixed) converges to the
+    oracle's direct-solve Newton solution."""
+    name = "cavity12_gr1e3"
+    cfg = synth.WORKLOADS[name]
+    prob, bc = oracle_problem(12, 12, 12, cfg["h"], cfg["Gr"], cfg["Pr"])
+    gam = synth.design(name)
+    xo, _ = S.newton(prob, gam, np.zeros((5, prob.g.Nn)), rtol=1e-12)
+    gp = nc.Problem.from_workload(name)
+    for mixed in (0, 1):
+        x = torch.zeros(gp.ndof, dtype=torch.float64, device="cuda")
+        _, info = gp.newton_solve(dev(gam), x, nc.default_opts(mixed=mixed, rtol_newton=1e-10))
+        assert info["status"] == "NC_OK"
+        assert rel(host(x), xo.ravel()) <= 1e-8, info
+
+
+def test_adjoint_and_sensitivity_match_oracle(nc):
+    """Flux-patch cavity at 8^3: adjoint solve and sensitivities against the
+    oracle's direct adjoint (the adjoint at the oracle's converged state)."""
+    n, Gr = 8, 1e4
+    prob, bc = oracle_problem(n, n, n, 1.0 / n, Gr, 0.71, patch_mode="flux")
+    gam = synth.smoothed_random(n, n, n, 1.0 / n, 3)
+    xo, _ = S.newton(prob, gam, np.zeros((5, prob.g.Nn)), rtol=1e-13)
+    phi, dphi = S.objective(prob, bc, xo)
+    lam_o = S.adjoint(prob, xo, gam, -dphi)
+    sens_o = S.sensitivity(prob, xo, gam, lam_o)
+    p = nc.make_params(n, n, n, 1.0 / n, Gr, 0.71, **synth.MATERIAL)
+    gp = nc.Problem(p, nc.cavity_bcs(nc.PATCH_FLUX, 1.0))
+    for mixed in (0, 1):
+        lam, info = gp.adjoint_solve(dev(xo), dev(gam), dev(-dphi),
+                                     opts=nc.default_opts(mixed=mixed))
+        assert rel(host(lam), lam_o.ravel()) <= 1e-7, info
+        sens = host(gp.sensitivity(dev(xo), dev(gam), lam))
+        assert rel(sens, sens_o) <= 1e-7
+
+
+def test_errors_are_status_codes(nc):
+    p = nc.make_params(4, 4, 4, 0.25, 1e3, 0.71)
+    gp = nc.Problem(p, nc.cavity_bcs())
+    x = torch.zeros(gp.ndof, dtype=torch.float64, device="cuda")
+    gam = torch.full((gp.E,), float("nan"), dtype=torch.float64, device="cuda")
+    _, info = gp.newton_solve(gam, x, check=False)
+    assert info["status"] == "NC_ERR_NAN"
+    # bad sizes -> NC_ERR_ARG without touching the device
+    bad = nc.make_params(0, 4, 4, 0.25, 1e3, 0.71)
+    ctx = nc._ctx()
+    import ctypes
+    assert nc.lib.nc_setup(ctypes.byref(bad), ctypes.byref(nc.cavity_bcs()), ctypes.byref(ctx)) == 1
+    assert nc.lib.nc_residual(gp.ctx, None, None, None, 0, None) == 1
