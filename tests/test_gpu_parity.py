@@ -138,7 +138,8 @@ def test_sensitivity_and_objective(nc, c):
     phi_o, g_o = S.objective(prob, bc, x)
     assert phi == pytest.approx(phi_o, rel=1e-13, abs=1e-15)
     assert np.array_equal(host(g, g_o.shape) != 0, g_o != 0)
-    assert rel(host(g, g_o.shape), g_o) <= 1e-15
+    if np.any(g_o):  # an empty patch (no face inside it) has a zero gradient
+        assert rel(host(g, g_o.shape), g_o) <= 1e-15
 
 
 def test_adjoint_dot_product_32cube(nc):
