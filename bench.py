@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--workload", default="fins64_gr1e4")
     ap.add_argument("--prec", default="f64", choices=["f64", "f32"])
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     return ap.parse_args()
 
 
@@ -276,7 +277,7 @@ def run_ours(args, rank, world):
 
     if rank != 0:
         return None
-    cpu = cpu_baseline(args.workload) if world == 1 else None
+    cpu = cpu_baseline(args.workload) if world == 1 and not args.no_cpu else None
     line = {"metric": "J·v GDOF/s and state+adjoint solve time, FP32-mixed vs FP64 at 1e-8 rel",
             "value": round(value, 4), "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t_step, 4), "higher_is_better": True,
