@@ -43,7 +43,8 @@ typedef enum {
   NC_ERR_OOM = 3,      /* device allocation failed */
   NC_ERR_NAN = 4,      /* a non-finite value appeared in a norm */
   NC_ERR_MAXIT = 5,    /* iteration limit reached before the tolerance */
-  NC_ERR_DIVERGED = 6  /* Newton line search found no decrease */
+  NC_ERR_DIVERGED = 6, /* Newton line search found no decrease */
+  NC_ERR_SIZE = 7      /* problem larger than the fixed scratch of nc_jvp_static */
 } nc_status;
 
 typedef enum { NC_FP64 = 0, NC_FP32 = 1 } nc_prec;
@@ -151,6 +152,29 @@ nc_status nc_objective(nc_ctx* ctx, const double* x, double* phi_host, double* d
  * adjoint lambda of J^T lambda = -dPhi/dx.  Output [E].  FP64 only. */
 nc_status nc_sensitivity(nc_ctx* ctx, const double* x, const double* gamma,
                          const double* lambda, double* dphidgamma, void* stream);
+
+/* Allocation-free J v.  The paper has no counterpart: this is a library
+ * convenience for callers that may not allocate device memory -- an application
+ * whose own memory pool has reserved the device and forbids other cudaMalloc
+ * calls, a plug-in that must not make allocations its host does not track, or a
+ * latency-bound loop that cannot afford the synchronisation cudaMalloc/cudaFree
+ * may cause.  It computes the same product as nc_jvp (Dirichlet handling
+ * included, no element source) without a context: the caller passes the
+ * parameters, boundary conditions, inputs and output (device pointers, same
+ * layouts and prec as nc_jvp), and the scratch is a fixed device array of
+ * NC_STATIC_SCRATCH_BYTES inside the library, held by every GPU that loads it
+ * until the process exits.  The problem must fit: round_up(Nn, 256) + 40 * E *
+ * sizeof(element) <= NC_STATIC_SCRATCH_BYTES (about 200,000 elements in FP64,
+ * 400,000 in FP32), else NC_ERR_SIZE and nothing is launched.  The first call on
+ * a device looks the array's device address up (once per device, with that
+ * device current); make that first call before any stream capture.  The array
+ * keeps the last call's contents; nothing in it needs to start at zero.  All
+ * calls share it, so calls whose work can overlap on the GPU (different streams
+ * or threads without ordering) race and must be serialised by the caller.
+ * Errors: NC_ERR_ARG (NULL pointer, bad sizes or ids), NC_ERR_SIZE, NC_ERR_CUDA. */
+#define NC_STATIC_SCRATCH_BYTES (64ull << 20)
+nc_status nc_jvp_static(const nc_params* prm, const nc_bcs* bcs, const void* x,
+                        const void* gamma, const void* v, void* Jv, int prec, void* stream);
 
 /* Solver options.  rtol_newton: stop when ||R|| <= rtol_newton ||R_0|| (Sec. 5.1);
  * rtol_lin: FGMRES relative tolerance per linear solve (Sec. 5.2); max_newton,

@@ -128,6 +128,7 @@ const char* nc_status_string(int st) {
     case NC_ERR_NAN: return "non-finite value";
     case NC_ERR_MAXIT: return "iteration limit reached";
     case NC_ERR_DIVERGED: return "Newton line search found no decrease";
+    case NC_ERR_SIZE: return "problem larger than the fixed scratch of nc_jvp_static";
     default: return "unknown status";
   }
 }

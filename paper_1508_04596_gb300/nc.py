@@ -26,7 +26,7 @@ VEL_NOSLIP, VEL_FREE, VEL_SYMMETRY = 0, 1, 2
 T_ADIABATIC, T_DIRICHLET = 0, 1
 PATCH_NONE, PATCH_DIRICHLET, PATCH_FLUX = 0, 1, 2
 STATUS = {0: "NC_OK", 1: "NC_ERR_ARG", 2: "NC_ERR_CUDA", 3: "NC_ERR_OOM", 4: "NC_ERR_NAN",
-          5: "NC_ERR_MAXIT", 6: "NC_ERR_DIVERGED"}
+          5: "NC_ERR_MAXIT", 6: "NC_ERR_DIVERGED", 7: "NC_ERR_SIZE"}
 
 
 class Params(ctypes.Structure):
