@@ -32,7 +32,7 @@ NAPPLY = 16  # J v applications per step
 # Operation counts per element (one +, -, * or / = 1 flop; an FMA = 2), of the
 # element routines in csrc/nc_element.cuh, counted by instantiating them with a
 # counting number type.
-FLOPS_PER_ELEM = {"residual": 6482, "jvp": 10386, "jtvp": 9938, "diag": 9093, "sens": 8146}
+FLOPS_PER_ELEM = {"residual": 3038, "jvp": 4950, "jtvp": 4718, "diag": 7293, "sens": 4281}
 # ALU peaks (whole GPU): FP32 = 152 SM x 128 lanes x 2 flop x 2.07 GHz; FP64 = the
 # GB300's nominal 1.25 TFLOP/s (equal to our FMA-chain probe on the box: 78.5 and
 # 1.25 TFLOP/s measured).

@@ -74,35 +74,80 @@ NC_HD constexpr double gfac(int i, int q) {
 }
 NC_HD constexpr double gsgn(int i) { return i ? 1.0 : -1.0; }
 
-// Value and physical gradient of one scalar nodal field at Gauss point (gx,gy,gz).
-template <typename R, int gx, int gy, int gz>
-NC_HD void interp(const R x[8], R inv_h, R& val, R grad[3]) {
-  R v = R(0), dx = R(0), dy = R(0), dz = R(0);
-#pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    const int ia = a & 1, ja = (a >> 1) & 1, ka = (a >> 2) & 1;
-    v += R(gfac(ia, gx) * gfac(ja, gy) * gfac(ka, gz)) * x[a];
-    dx += R(gsgn(ia) * gfac(ja, gy) * gfac(ka, gz)) * x[a];
-    dy += R(gfac(ia, gx) * gsgn(ja) * gfac(ka, gz)) * x[a];
-    dz += R(gfac(ia, gx) * gfac(ja, gy) * gsgn(ka)) * x[a];
-  }
-  val = v;
-  grad[0] = dx * inv_h;
-  grad[1] = dy * inv_h;
-  grad[2] = dz * inv_h;
+// Interpolation to a pair of Gauss points.  The 8 points are processed in four
+// pairs (qy, qz) in {0,1}^2, each pair holding qx = 0 and qx = 1.  Along each
+// axis a Q1 field at a Gauss point is a linear interpolation x0 + c (x1 - x0)
+// with c = GW[q] (the shape-function weight of the "+" node), and the same
+// difference (x1 - x0) is the derivative along that axis, so values and
+// gradients share their differences (a tensor-product factorisation of the
+// 2x2x2 rule).  Gradients carry 1/h.
+constexpr double GW0 = 0.21132486540518711775;  // (1 - 1/sqrt 3)/2: weight of node 1 at point 0
+constexpr double GW1 = 0.78867513459481288225;  // (1 + 1/sqrt 3)/2: weight of node 1 at point 1
+NC_HD constexpr double gw(int q) { return q ? GW1 : GW0; }
+
+template <typename R, int qy, int qz>
+NC_HD void interp_pair(const R x[8], R inv_h, R val[2], R& gx, R gy[2], R gz[2]) {
+  const R cy = R(gw(qy)), cz = R(gw(qz)), c0 = R(GW0), c1 = R(GW1);
+  // z differences and interpolation at qz; index [ia][ja] <-> a = ia + 2 ja (+4 ka)
+  const R dz00 = x[4] - x[0], dz10 = x[5] - x[1], dz01 = x[6] - x[2], dz11 = x[7] - x[3];
+  const R z00 = x[0] + cz * dz00, z10 = x[1] + cz * dz10;
+  const R z01 = x[2] + cz * dz01, z11 = x[3] + cz * dz11;
+  // y differences and interpolation at qy, per ia
+  const R dy0 = z01 - z00, dy1 = z11 - z10;
+  const R y0 = z00 + cy * dy0, y1 = z10 + cy * dy1;
+  // x
+  const R dx = y1 - y0;
+  val[0] = y0 + c0 * dx;
+  val[1] = y0 + c1 * dx;
+  gx = dx * inv_h;
+  const R ddy = dy1 - dy0;
+  gy[0] = (dy0 + c0 * ddy) * inv_h;
+  gy[1] = (dy0 + c1 * ddy) * inv_h;
+  const R zy0 = dz00 + cy * (dz01 - dz00), zy1 = dz10 + cy * (dz11 - dz10);
+  const R ddz = zy1 - zy0;
+  gz[0] = (zy0 + c0 * ddz) * inv_h;
+  gz[1] = (zy0 + c1 * ddz) * inv_h;
 }
 
-// out[a] += N_a(g) f0 + d_j N_a(g) F1[j]   (F1 already carries 1/h)
-template <typename R, int gx, int gy, int gz>
-NC_HD void test_accum(R out[8], R f0, const R F1[3]) {
-#pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    const int ia = a & 1, ja = (a >> 1) & 1, ka = (a >> 2) & 1;
-    out[a] += R(gfac(ia, gx) * gfac(ja, gy) * gfac(ka, gz)) * f0 +
-              R(gsgn(ia) * gfac(ja, gy) * gfac(ka, gz)) * F1[0] +
-              R(gfac(ia, gx) * gsgn(ja) * gfac(ka, gz)) * F1[1] +
-              R(gfac(ia, gx) * gfac(ja, gy) * gsgn(ka)) * F1[2];
-  }
+// Transpose of interp_pair (without the 1/h, which the caller folds into F1):
+// out[a] += sum_qx [ N_a f0[qx] + dN_a/dxi_j F1[qx][j] ] over the pair.
+template <typename R, int qy, int qz>
+NC_HD void test_pair(R out[8], const R f0[2], const R F1[2][3]) {
+  const R cy = R(gw(qy)), cz = R(gw(qz)), c0 = R(GW0), c1 = R(GW1);
+  // cotangents of val[], gx, gy[], gz[]
+  const R gzb0 = F1[0][2], gzb1 = F1[1][2];
+  const R gyb0 = F1[0][1], gyb1 = F1[1][1];
+  const R gxb = F1[0][0] + F1[1][0];
+  // gz[q] = zy0 + c_q ddz ; ddz = zy1 - zy0
+  const R ddzb = c0 * gzb0 + c1 * gzb1;
+  const R zy0b = gzb0 + gzb1 - ddzb, zy1b = ddzb;
+  // gy[q] = dy0 + c_q ddy ; ddy = dy1 - dy0
+  const R ddyb = c0 * gyb0 + c1 * gyb1;
+  R dy0b = gyb0 + gyb1 - ddyb, dy1b = ddyb;
+  // val[q] = y0 + c_q dx ; gx = dx ; dx = y1 - y0
+  const R dxb = c0 * f0[0] + c1 * f0[1] + gxb;
+  const R y0b = f0[0] + f0[1] - dxb, y1b = dxb;
+  // y0 = z00 + cy dy0 ; y1 = z10 + cy dy1
+  dy0b += cy * y0b;
+  dy1b += cy * y1b;
+  // dy0 = z01 - z00 ; dy1 = z11 - z10
+  const R z00b = y0b - dy0b, z01b = dy0b, z10b = y1b - dy1b, z11b = dy1b;
+  // zy0 = dz00 + cy (dz01 - dz00) ; zy1 likewise
+  R dz00b = zy0b - cy * zy0b, dz01b = cy * zy0b, dz10b = zy1b - cy * zy1b, dz11b = cy * zy1b;
+  // z.. = x[..] + cz dz..
+  dz00b += cz * z00b;
+  dz10b += cz * z10b;
+  dz01b += cz * z01b;
+  dz11b += cz * z11b;
+  // dz.. = x[top] - x[bottom]
+  out[0] += z00b - dz00b;
+  out[1] += z10b - dz10b;
+  out[2] += z01b - dz01b;
+  out[3] += z11b - dz11b;
+  out[4] += dz00b;
+  out[5] += dz10b;
+  out[6] += dz01b;
+  out[7] += dz11b;
 }
 
 // Quadrature-point state: u, G[i][j] = d_j u_i, p, grad p, T, grad T.
@@ -111,13 +156,68 @@ struct QP {
   R u[3], G[3][3], p, gp[3], T, gT[3];
 };
 
-template <typename R, int gx, int gy, int gz>
-NC_HD void interp_all(const R xe[5][8], R inv_h, QP<R>& q) {
-  interp<R, gx, gy, gz>(xe[0], inv_h, q.u[0], q.G[0]);
-  interp<R, gx, gy, gz>(xe[1], inv_h, q.u[1], q.G[1]);
-  interp<R, gx, gy, gz>(xe[2], inv_h, q.u[2], q.G[2]);
-  interp<R, gx, gy, gz>(xe[3], inv_h, q.p, q.gp);
-  interp<R, gx, gy, gz>(xe[4], inv_h, q.T, q.gT);
+template <typename R, int qy, int qz>
+NC_HD void interp_field_pair(const R x[8], R inv_h, R v[2], R g[2][3]) {
+  R val[2], gx, gy[2], gz[2];
+  interp_pair<R, qy, qz>(x, inv_h, val, gx, gy, gz);
+  v[0] = val[0];
+  v[1] = val[1];
+  g[0][0] = gx;
+  g[1][0] = gx;
+  g[0][1] = gy[0];
+  g[1][1] = gy[1];
+  g[0][2] = gz[0];
+  g[1][2] = gz[1];
+}
+
+template <typename R, int qy, int qz>
+NC_HD void interp_all_pair(const R xe[5][8], R inv_h, QP<R> q[2]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    R v[2], g[2][3];
+    interp_field_pair<R, qy, qz>(xe[i], inv_h, v, g);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      q[s].u[i] = v[s];
+      q[s].G[i][0] = g[s][0];
+      q[s].G[i][1] = g[s][1];
+      q[s].G[i][2] = g[s][2];
+    }
+  }
+  {
+    R v[2], g[2][3];
+    interp_field_pair<R, qy, qz>(xe[3], inv_h, v, g);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      q[s].p = v[s];
+      q[s].gp[0] = g[s][0];
+      q[s].gp[1] = g[s][1];
+      q[s].gp[2] = g[s][2];
+    }
+  }
+  {
+    R v[2], g[2][3];
+    interp_field_pair<R, qy, qz>(xe[4], inv_h, v, g);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      q[s].T = v[s];
+      q[s].gT[0] = g[s][0];
+      q[s].gT[1] = g[s][1];
+      q[s].gT[2] = g[s][2];
+    }
+  }
+}
+
+// out[f] += test-side contributions of the pair for all five fields.
+template <typename R, int qy, int qz>
+NC_HD void test_all_pair(R out[5][8], const R f0[2][5], const R F1[2][5][3]) {
+#pragma unroll
+  for (int f = 0; f < 5; ++f) {
+    const R a[2] = {f0[0][f], f0[1][f]};
+    const R b[2][3] = {{F1[0][f][0], F1[0][f][1], F1[0][f][2]},
+                       {F1[1][f][0], F1[1][f][1], F1[1][f][2]}};
+    test_pair<R, qy, qz>(out[f], a, b);
+  }
 }
 
 // Element coefficients shared by all Gauss points.
@@ -156,55 +256,62 @@ NC_HD void strong(const QP<R>& q, const ElemCoef<R>& k, const ElemConst<R>& c, R
 }
 
 // ---------------------------------------------------------------------------- residual
-template <typename R, int g>
-NC_HD void gp_residual(const R xe[5][8], const ElemCoef<R>& k, const ElemConst<R>& c,
-                       R out[5][8]) {
-  constexpr int gx = g & 1, gy = (g >> 1) & 1, gz = (g >> 2) & 1;
-  QP<R> q;
-  interp_all<R, gx, gy, gz>(xe, c.inv_h, q);
+// Pointwise fluxes of the residual: w-scaled f0 and (w/h)-scaled F1.
+template <typename R>
+NC_HD void flux_residual(const QP<R>& q, const ElemCoef<R>& k, const ElemConst<R>& c, R f0[5],
+                         R F1[5][3]) {
   R conv[3], rM[3], rT;
   strong(q, k, c, conv, rM, rT);
   const R w = c.wq, wh = c.wq * c.inv_h;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    R F1[3];
+    const R trM = k.tau * rM[i];
 #pragma unroll
     for (int j = 0; j < 3; ++j)
-      F1[j] = wh * (c.Pr * (q.G[i][j] + q.G[j][i]) - (i == j ? q.p : R(0)) + k.tau * q.u[j] * rM[i]);
-    test_accum<R, gx, gy, gz>(out[i], w * (conv[i] + k.alpha * q.u[i] + c.beta * c.eg[i] * q.T), F1);
+      F1[i][j] = wh * (c.Pr * (q.G[i][j] + q.G[j][i]) - (i == j ? q.p : R(0)) + q.u[j] * trM);
+    f0[i] = w * (conv[i] + k.alpha * q.u[i] + c.beta * c.eg[i] * q.T);
   }
-  {
-    R F1[3] = {wh * k.tau * rM[0], wh * k.tau * rM[1], wh * k.tau * rM[2]};
-    test_accum<R, gx, gy, gz>(out[3], w * (q.G[0][0] + q.G[1][1] + q.G[2][2]), F1);
-  }
-  {
-    R F1[3];
+  f0[3] = w * (q.G[0][0] + q.G[1][1] + q.G[2][2]);
 #pragma unroll
-    for (int j = 0; j < 3; ++j) F1[j] = wh * (k.K * q.gT[j] + k.tauT * q.u[j] * rT);
-    test_accum<R, gx, gy, gz>(out[4], w * rT, F1);
-  }
+  for (int j = 0; j < 3; ++j) F1[3][j] = wh * k.tau * rM[j];
+  f0[4] = w * rT;
+  const R trT = k.tauT * rT;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) F1[4][j] = wh * (k.K * q.gT[j] + q.u[j] * trT);
+}
+
+template <typename R, int qy, int qz>
+NC_HD void pair_residual(const R xe[5][8], const ElemCoef<R>& k, const ElemConst<R>& c,
+                         R out[5][8]) {
+  QP<R> q[2];
+  interp_all_pair<R, qy, qz>(xe, c.inv_h, q);
+  R f0[2][5], F1[2][5][3];
+  flux_residual(q[0], k, c, f0[0], F1[0]);
+  flux_residual(q[1], k, c, f0[1], F1[1]);
+  test_all_pair<R, qy, qz>(out, f0, F1);
+}
+
+template <typename R>
+NC_HD void zero_out(R out[5][8]) {
+#pragma unroll
+  for (int f = 0; f < 5; ++f)
+#pragma unroll
+    for (int a = 0; a < 8; ++a) out[f][a] = R(0);
 }
 
 template <typename R>
 NC_HD void elem_residual(const R xe[5][8], R gam, R s, const ElemConst<R>& c, R out[5][8]) {
   R S;
   ElemCoef<R> k = elem_coef(xe, gam, s, c, S);
-#pragma unroll
-  for (int f = 0; f < 5; ++f)
-#pragma unroll
-    for (int a = 0; a < 8; ++a) out[f][a] = R(0);
-  gp_residual<R, 0>(xe, k, c, out);
-  gp_residual<R, 1>(xe, k, c, out);
-  gp_residual<R, 2>(xe, k, c, out);
-  gp_residual<R, 3>(xe, k, c, out);
-  gp_residual<R, 4>(xe, k, c, out);
-  gp_residual<R, 5>(xe, k, c, out);
-  gp_residual<R, 6>(xe, k, c, out);
-  gp_residual<R, 7>(xe, k, c, out);
+  zero_out(out);
+  pair_residual<R, 0, 0>(xe, k, c, out);
+  pair_residual<R, 1, 0>(xe, k, c, out);
+  pair_residual<R, 0, 1>(xe, k, c, out);
+  pair_residual<R, 1, 1>(xe, k, c, out);
 }
 
 // ---------------------------------------------------------------------------- tangent
-// Directional derivative of the pointwise fluxes in the state direction dq and
+// Directional derivative of the pointwise fluxes in the state direction d and
 // the parameter directions (dalpha, dK, dtau, dtauT); returns w-scaled f0 and
 // (w/h)-scaled F1.
 template <typename R>
@@ -225,32 +332,34 @@ NC_HD void flux_tangent(const QP<R>& q, const QP<R>& d, const ElemCoef<R>& k, R 
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     f0[i] = w * (dconv[i] + k.alpha * d.u[i] + dalpha * q.u[i] + c.beta * c.eg[i] * d.T);
+    // d(tau u_j rM_i) = u_j (dtau rM_i + tau drM_i) + d.u_j (tau rM_i)
+    const R a = dtau * rM[i] + k.tau * drM[i];
+    const R b = k.tau * rM[i];
 #pragma unroll
     for (int j = 0; j < 3; ++j)
-      F1[i][j] = wh * (c.Pr * (d.G[i][j] + d.G[j][i]) - (i == j ? d.p : R(0)) +
-                       dtau * q.u[j] * rM[i] + k.tau * (d.u[j] * rM[i] + q.u[j] * drM[i]));
+      F1[i][j] = wh * (c.Pr * (d.G[i][j] + d.G[j][i]) - (i == j ? d.p : R(0)) + q.u[j] * a +
+                       d.u[j] * b);
   }
   f0[3] = w * (d.G[0][0] + d.G[1][1] + d.G[2][2]);
 #pragma unroll
   for (int j = 0; j < 3; ++j) F1[3][j] = wh * (dtau * rM[j] + k.tau * drM[j]);
   f0[4] = w * drT;
+  const R aT = dtauT * rT + k.tauT * drT, bT = k.tauT * rT;
 #pragma unroll
   for (int j = 0; j < 3; ++j)
-    F1[4][j] = wh * (k.K * d.gT[j] + dK * q.gT[j] + dtauT * q.u[j] * rT +
-                     k.tauT * (d.u[j] * rT + q.u[j] * drT));
+    F1[4][j] = wh * (k.K * d.gT[j] + dK * q.gT[j] + q.u[j] * aT + d.u[j] * bT);
 }
 
-template <typename R, int g>
-NC_HD void gp_jvp(const R xe[5][8], const R ve[5][8], const ElemCoef<R>& k, R dtau, R dtauT,
-                  const ElemConst<R>& c, R out[5][8]) {
-  constexpr int gx = g & 1, gy = (g >> 1) & 1, gz = (g >> 2) & 1;
-  QP<R> q, d;
-  interp_all<R, gx, gy, gz>(xe, c.inv_h, q);
-  interp_all<R, gx, gy, gz>(ve, c.inv_h, d);
-  R f0[5], F1[5][3];
-  flux_tangent(q, d, k, R(0), R(0), dtau, dtauT, c, f0, F1);
-#pragma unroll
-  for (int f = 0; f < 5; ++f) test_accum<R, gx, gy, gz>(out[f], f0[f], F1[f]);
+template <typename R, int qy, int qz>
+NC_HD void pair_jvp(const R xe[5][8], const R ve[5][8], const ElemCoef<R>& k, R dtau, R dtauT,
+                    const ElemConst<R>& c, R out[5][8]) {
+  QP<R> q[2], d[2];
+  interp_all_pair<R, qy, qz>(xe, c.inv_h, q);
+  interp_all_pair<R, qy, qz>(ve, c.inv_h, d);
+  R f0[2][5], F1[2][5][3];
+  flux_tangent(q[0], d[0], k, R(0), R(0), dtau, dtauT, c, f0[0], F1[0]);
+  flux_tangent(q[1], d[1], k, R(0), R(0), dtau, dtauT, c, f0[1], F1[1]);
+  test_all_pair<R, qy, qz>(out, f0, F1);
 }
 
 // J_e v_e including the dtau/du_e and dtau_T/du_e terms (App. B).
@@ -267,34 +376,23 @@ NC_HD void elem_jvp(const R xe[5][8], const R ve[5][8], R gam, R s, const ElemCo
   // d tau = -1/2 tau^3 d(S/(16h^2)),  dS = 2 u_e.v_e
   const R dtau = -k.tau * k.tau * k.tau * c.inv16h2 * uv;
   const R dtauT = -k.tauT * k.tauT * k.tauT * c.inv16h2 * uv;
-#pragma unroll
-  for (int f = 0; f < 5; ++f)
-#pragma unroll
-    for (int a = 0; a < 8; ++a) out[f][a] = R(0);
-  gp_jvp<R, 0>(xe, ve, k, dtau, dtauT, c, out);
-  gp_jvp<R, 1>(xe, ve, k, dtau, dtauT, c, out);
-  gp_jvp<R, 2>(xe, ve, k, dtau, dtauT, c, out);
-  gp_jvp<R, 3>(xe, ve, k, dtau, dtauT, c, out);
-  gp_jvp<R, 4>(xe, ve, k, dtau, dtauT, c, out);
-  gp_jvp<R, 5>(xe, ve, k, dtau, dtauT, c, out);
-  gp_jvp<R, 6>(xe, ve, k, dtau, dtauT, c, out);
-  gp_jvp<R, 7>(xe, ve, k, dtau, dtauT, c, out);
+  zero_out(out);
+  pair_jvp<R, 0, 0>(xe, ve, k, dtau, dtauT, c, out);
+  pair_jvp<R, 1, 0>(xe, ve, k, dtau, dtauT, c, out);
+  pair_jvp<R, 0, 1>(xe, ve, k, dtau, dtauT, c, out);
+  pair_jvp<R, 1, 1>(xe, ve, k, dtau, dtauT, c, out);
 }
 
 // ---------------------------------------------------------------------------- adjoint
-// Given the interpolated test field w (value c0 and gradient C1 per field at the
-// point), accumulate (dFlux/dq)^T (c0, C1) into the element output and return the
-// cotangents of tau and tau_T.
-template <typename R, int g>
-NC_HD void gp_jtvp(const R xe[5][8], const R we[5][8], const ElemCoef<R>& k,
-                   const ElemConst<R>& c, R out[5][8], R& tau_bar, R& tauT_bar) {
-  constexpr int gx = g & 1, gy = (g >> 1) & 1, gz = (g >> 2) & 1;
-  QP<R> q, t;
-  interp_all<R, gx, gy, gz>(xe, c.inv_h, q);
-  interp_all<R, gx, gy, gz>(we, c.inv_h, t);
+// Given the interpolated test field t (value and gradient per field at the
+// point), the cotangents of the point state, (dFlux/dq)^T (w t), returned as
+// f0 (value slots) and F1 (gradient slots, times 1/h) for the test-side
+// transpose, plus the cotangents of tau and tau_T accumulated.
+template <typename R>
+NC_HD void flux_adjoint(const QP<R>& q, const QP<R>& t, const ElemCoef<R>& k,
+                        const ElemConst<R>& c, R f0[5], R F1[5][3], R& tau_bar, R& tauT_bar) {
   R conv[3], rM[3], rT;
   strong(q, k, c, conv, rM, rT);
-  // cotangents of the fluxes: c0 = w * test value, C1 = w * test gradient
   const R w = c.wq;
   R c0[5] = {w * t.u[0], w * t.u[1], w * t.u[2], w * t.p, w * t.T};
   R C1[5][3];
@@ -306,7 +404,7 @@ NC_HD void gp_jtvp(const R xe[5][8], const R we[5][8], const ElemCoef<R>& k,
     C1[3][j] = w * t.gp[j];
     C1[4][j] = w * t.gT[j];
   }
-  R rMb[3], ub[3], Gb[3][3], gpb[3], gTb[3];
+  R rMb[3], ub[3], Gb[3][3], gTb[3];
   const R C4u = C1[4][0] * q.u[0] + C1[4][1] * q.u[1] + C1[4][2] * q.u[2];
   const R rTb = c0[4] + k.tauT * C4u;
   R tb = R(0);
@@ -314,17 +412,18 @@ NC_HD void gp_jtvp(const R xe[5][8], const R we[5][8], const ElemCoef<R>& k,
   for (int i = 0; i < 3; ++i) {
     const R Ciu = C1[i][0] * q.u[0] + C1[i][1] * q.u[1] + C1[i][2] * q.u[2];
     rMb[i] = k.tau * (Ciu + C1[3][i]);
-    tb += Ciu * rM[i] + C1[3][i] * rM[i];
+    tb += (Ciu + C1[3][i]) * rM[i];
   }
   tau_bar += tb;
   tauT_bar += C4u * rT;
-  R pb = -(C1[0][0] + C1[1][1] + C1[2][2]);
+  const R pb = -(C1[0][0] + C1[1][1] + C1[2][2]);
   R Tb = R(0);
+  const R trT = k.tauT * rT;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    ub[j] = k.tau * (C1[0][j] * rM[0] + C1[1][j] * rM[1] + C1[2][j] * rM[2]) + k.tauT * C1[4][j] * rT;
+    ub[j] = k.tau * (C1[0][j] * rM[0] + C1[1][j] * rM[1] + C1[2][j] * rM[2]) + C1[4][j] * trT +
+            rTb * q.gT[j];
     gTb[j] = k.K * C1[4][j] + rTb * q.u[j];
-    gpb[j] = rMb[j];
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -342,22 +441,34 @@ NC_HD void gp_jtvp(const R xe[5][8], const R we[5][8], const ElemCoef<R>& k,
       Gb[i][j] += cb * q.u[j];
     }
   }
-#pragma unroll
-  for (int j = 0; j < 3; ++j) ub[j] += rTb * q.gT[j];
   const R ih = c.inv_h;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    R F1[3] = {Gb[i][0] * ih, Gb[i][1] * ih, Gb[i][2] * ih};
-    test_accum<R, gx, gy, gz>(out[i], ub[i], F1);
+    f0[i] = ub[i];
+    F1[i][0] = Gb[i][0] * ih;
+    F1[i][1] = Gb[i][1] * ih;
+    F1[i][2] = Gb[i][2] * ih;
   }
-  {
-    R F1[3] = {gpb[0] * ih, gpb[1] * ih, gpb[2] * ih};
-    test_accum<R, gx, gy, gz>(out[3], pb, F1);
-  }
-  {
-    R F1[3] = {gTb[0] * ih, gTb[1] * ih, gTb[2] * ih};
-    test_accum<R, gx, gy, gz>(out[4], Tb, F1);
-  }
+  f0[3] = pb;
+  F1[3][0] = rMb[0] * ih;
+  F1[3][1] = rMb[1] * ih;
+  F1[3][2] = rMb[2] * ih;
+  f0[4] = Tb;
+  F1[4][0] = gTb[0] * ih;
+  F1[4][1] = gTb[1] * ih;
+  F1[4][2] = gTb[2] * ih;
+}
+
+template <typename R, int qy, int qz>
+NC_HD void pair_jtvp(const R xe[5][8], const R we[5][8], const ElemCoef<R>& k,
+                     const ElemConst<R>& c, R out[5][8], R& tau_bar, R& tauT_bar) {
+  QP<R> q[2], t[2];
+  interp_all_pair<R, qy, qz>(xe, c.inv_h, q);
+  interp_all_pair<R, qy, qz>(we, c.inv_h, t);
+  R f0[2][5], F1[2][5][3];
+  flux_adjoint(q[0], t[0], k, c, f0[0], F1[0], tau_bar, tauT_bar);
+  flux_adjoint(q[1], t[1], k, c, f0[1], F1[1], tau_bar, tauT_bar);
+  test_all_pair<R, qy, qz>(out, f0, F1);
 }
 
 // J_e^T w_e.
@@ -366,19 +477,12 @@ NC_HD void elem_jtvp(const R xe[5][8], const R we[5][8], R gam, R s, const ElemC
                      R out[5][8]) {
   R S;
   ElemCoef<R> k = elem_coef(xe, gam, s, c, S);
-#pragma unroll
-  for (int f = 0; f < 5; ++f)
-#pragma unroll
-    for (int a = 0; a < 8; ++a) out[f][a] = R(0);
+  zero_out(out);
   R tb = R(0), tbT = R(0);
-  gp_jtvp<R, 0>(xe, we, k, c, out, tb, tbT);
-  gp_jtvp<R, 1>(xe, we, k, c, out, tb, tbT);
-  gp_jtvp<R, 2>(xe, we, k, c, out, tb, tbT);
-  gp_jtvp<R, 3>(xe, we, k, c, out, tb, tbT);
-  gp_jtvp<R, 4>(xe, we, k, c, out, tb, tbT);
-  gp_jtvp<R, 5>(xe, we, k, c, out, tb, tbT);
-  gp_jtvp<R, 6>(xe, we, k, c, out, tb, tbT);
-  gp_jtvp<R, 7>(xe, we, k, c, out, tb, tbT);
+  pair_jtvp<R, 0, 0>(xe, we, k, c, out, tb, tbT);
+  pair_jtvp<R, 1, 0>(xe, we, k, c, out, tb, tbT);
+  pair_jtvp<R, 0, 1>(xe, we, k, c, out, tb, tbT);
+  pair_jtvp<R, 1, 1>(xe, we, k, c, out, tb, tbT);
   // tau(S), S = u_e^T u_e:  d tau/d u_e = -tau^3/(16 h^2) u_e  (App. B)
   const R gsum = -(k.tau * k.tau * k.tau * tb + k.tauT * k.tauT * k.tauT * tbT) * c.inv16h2;
 #pragma unroll
@@ -388,13 +492,10 @@ NC_HD void elem_jtvp(const R xe[5][8], const R we[5][8], R gam, R s, const ElemC
 }
 
 // ---------------------------------------------------------------------------- design derivative
-template <typename R, int g>
-NC_HD R gp_sens(const R xe[5][8], const R le[5][8], const ElemCoef<R>& k, R dalpha, R dK,
-                R dtau, R dtauT, const ElemConst<R>& c) {
-  constexpr int gx = g & 1, gy = (g >> 1) & 1, gz = (g >> 2) & 1;
-  QP<R> q, t, zero;
-  interp_all<R, gx, gy, gz>(xe, c.inv_h, q);
-  interp_all<R, gx, gy, gz>(le, c.inv_h, t);
+template <typename R>
+NC_HD R point_sens(const QP<R>& q, const QP<R>& t, const ElemCoef<R>& k, R dalpha, R dK, R dtau,
+                   R dtauT, const ElemConst<R>& c) {
+  QP<R> zero;
   zero.p = zero.T = R(0);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -404,14 +505,25 @@ NC_HD R gp_sens(const R xe[5][8], const R le[5][8], const ElemCoef<R>& k, R dalp
   }
   R f0[5], F1[5][3];
   flux_tangent(q, zero, k, dalpha, dK, dtau, dtauT, c, f0, F1);
-  // F1 carries w/h; the test gradient below is the physical one times h
+  // F1 carries w/h; the test gradient t carries 1/h: multiply by h once
   const R h = R(1) / c.inv_h;
   R acc = f0[0] * t.u[0] + f0[1] * t.u[1] + f0[2] * t.u[2] + f0[3] * t.p + f0[4] * t.T;
+  R acc1 = R(0);
 #pragma unroll
   for (int j = 0; j < 3; ++j)
-    acc += (F1[0][j] * t.G[0][j] + F1[1][j] * t.G[1][j] + F1[2][j] * t.G[2][j] +
-            F1[3][j] * t.gp[j] + F1[4][j] * t.gT[j]) * h;
-  return acc;
+    acc1 += F1[0][j] * t.G[0][j] + F1[1][j] * t.G[1][j] + F1[2][j] * t.G[2][j] +
+            F1[3][j] * t.gp[j] + F1[4][j] * t.gT[j];
+  return acc + acc1 * h;
+}
+
+template <typename R, int qy, int qz>
+NC_HD R pair_sens(const R xe[5][8], const R le[5][8], const ElemCoef<R>& k, R dalpha, R dK,
+                  R dtau, R dtauT, const ElemConst<R>& c) {
+  QP<R> q[2], t[2];
+  interp_all_pair<R, qy, qz>(xe, c.inv_h, q);
+  interp_all_pair<R, qy, qz>(le, c.inv_h, t);
+  return point_sens(q[0], t[0], k, dalpha, dK, dtau, dtauT, c) +
+         point_sens(q[1], t[1], k, dalpha, dK, dtau, dtauT, c);
 }
 
 // lambda_e^T d r_e / d gamma_e, through alpha_e, K_e, tau(alpha_e), tau_T(K_e).
@@ -424,15 +536,10 @@ NC_HD R elem_sens(const R xe[5][8], const R le[5][8], R gam, R s, const ElemCons
   const R dtau = -k.tau * k.tau * k.tau * k.alpha * da;
   // tau_T^-2 = S/(16h^2) + K^2 (4/h^2)^2   ->  dtau_T = -tau_T^3 K k2c dK
   const R dtauT = -k.tauT * k.tauT * k.tauT * k.K * c.k2c * dK;
-  R acc = R(0);
-  acc += gp_sens<R, 0>(xe, le, k, da, dK, dtau, dtauT, c);
-  acc += gp_sens<R, 1>(xe, le, k, da, dK, dtau, dtauT, c);
-  acc += gp_sens<R, 2>(xe, le, k, da, dK, dtau, dtauT, c);
-  acc += gp_sens<R, 3>(xe, le, k, da, dK, dtau, dtauT, c);
-  acc += gp_sens<R, 4>(xe, le, k, da, dK, dtau, dtauT, c);
-  acc += gp_sens<R, 5>(xe, le, k, da, dK, dtau, dtauT, c);
-  acc += gp_sens<R, 6>(xe, le, k, da, dK, dtau, dtauT, c);
-  acc += gp_sens<R, 7>(xe, le, k, da, dK, dtau, dtauT, c);
+  R acc = pair_sens<R, 0, 0>(xe, le, k, da, dK, dtau, dtauT, c);
+  acc += pair_sens<R, 1, 0>(xe, le, k, da, dK, dtau, dtauT, c);
+  acc += pair_sens<R, 0, 1>(xe, le, k, da, dK, dtau, dtauT, c);
+  acc += pair_sens<R, 1, 1>(xe, le, k, da, dK, dtau, dtauT, c);
   return acc;
 }
 
@@ -440,12 +547,9 @@ NC_HD R elem_sens(const R xe[5][8], const R le[5][8], R gam, R s, const ElemCons
 // diag(J_e): the (a,f),(a,f) entries, from the diagonal blocks of the flux
 // derivative (value slot and gradient slot of the same field) plus the tau
 // coupling of the velocity rows.
-template <typename R, int g>
-NC_HD void gp_diag(const R xe[5][8], const ElemCoef<R>& k, const ElemConst<R>& c, R out[5][8],
-                   R tcoup[3][8]) {
-  constexpr int gx = g & 1, gy = (g >> 1) & 1, gz = (g >> 2) & 1;
-  QP<R> q;
-  interp_all<R, gx, gy, gz>(xe, c.inv_h, q);
+template <typename R, int gx, int gy, int gz>
+NC_HD void point_diag(const QP<R>& q, const ElemCoef<R>& k, const ElemConst<R>& c, R out[5][8],
+                      R tcoup[3][8]) {
   R conv[3], rM[3], rT;
   strong(q, k, c, conv, rM, rT);
   const R w = c.wq, ih = c.inv_h;
@@ -470,27 +574,29 @@ NC_HD void gp_diag(const R xe[5][8], const ElemCoef<R>& k, const ElemConst<R>& c
   }
 }
 
+template <typename R, int qy, int qz>
+NC_HD void pair_diag(const R xe[5][8], const ElemCoef<R>& k, const ElemConst<R>& c, R out[5][8],
+                     R tcoup[3][8]) {
+  QP<R> q[2];
+  interp_all_pair<R, qy, qz>(xe, c.inv_h, q);
+  point_diag<R, 0, qy, qz>(q[0], k, c, out, tcoup);
+  point_diag<R, 1, qy, qz>(q[1], k, c, out, tcoup);
+}
+
 template <typename R>
 NC_HD void elem_diag(const R xe[5][8], R gam, R s, const ElemConst<R>& c, R out[5][8]) {
   R S;
   ElemCoef<R> k = elem_coef(xe, gam, s, c, S);
   R tc[3][8];
-#pragma unroll
-  for (int f = 0; f < 5; ++f)
-#pragma unroll
-    for (int a = 0; a < 8; ++a) out[f][a] = R(0);
+  zero_out(out);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int a = 0; a < 8; ++a) tc[i][a] = R(0);
-  gp_diag<R, 0>(xe, k, c, out, tc);
-  gp_diag<R, 1>(xe, k, c, out, tc);
-  gp_diag<R, 2>(xe, k, c, out, tc);
-  gp_diag<R, 3>(xe, k, c, out, tc);
-  gp_diag<R, 4>(xe, k, c, out, tc);
-  gp_diag<R, 5>(xe, k, c, out, tc);
-  gp_diag<R, 6>(xe, k, c, out, tc);
-  gp_diag<R, 7>(xe, k, c, out, tc);
+  pair_diag<R, 0, 0>(xe, k, c, out, tc);
+  pair_diag<R, 1, 0>(xe, k, c, out, tc);
+  pair_diag<R, 0, 1>(xe, k, c, out, tc);
+  pair_diag<R, 1, 1>(xe, k, c, out, tc);
   // d tau / d u_{a,i} = -tau^3/(16h^2) u_{a,i}
   const R dt = -k.tau * k.tau * k.tau * c.inv16h2;
 #pragma unroll
