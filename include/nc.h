@@ -181,7 +181,8 @@ nc_status nc_jvp_static(const nc_params* prm, const nc_bcs* bcs, const void* x,
  * max_lin (total FGMRES iterations per linear solve), restart (FGMRES restart,
  * <= 64); mg_levels: multigrid levels to use (0 = all); smooth_its: Jacobi-GMRES
  * smoothing iterations per pre/post step; coarse_its: Jacobi-GMRES iterations on
- * the coarsest level; mixed: 1 = Jacobian products, smoother and coarse levels
+ * the coarsest level when it has more than 1000 unknowns (smaller coarsest levels
+ * are solved with a dense inverse formed once per linearisation); mixed: 1 = Jacobian products, smoother and coarse levels
  * in FP32 inside FP64 Newton / refinement, 0 = everything FP64; ramp_steps: on
  * Newton failure from the given start, retry with the buoyancy (Gr) ramped up
  * in this many geometric steps (0 = no ramping; the paper ramps the heat load,
@@ -202,7 +203,7 @@ typedef struct {
 } nc_solve_info;
 
 /* Fill opts with defaults (rtol_newton 1e-8, rtol_lin 1e-5, max_newton 30,
- * max_lin 200, restart 30, all levels, smooth_its 2, coarse_its 30, mixed 1,
+ * max_lin 200, restart 30, all levels, smooth_its 4, coarse_its 30, mixed 1,
  * ramp_steps 0). */
 void nc_default_opts(nc_solve_opts* opts);
 

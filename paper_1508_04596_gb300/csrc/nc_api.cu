@@ -111,6 +111,10 @@ void free_level(Level& L) {
   cudaFree(L.f64.Hd);
   cudaFree(L.f32.Hd);
   L.f64.Hd = L.f32.Hd = nullptr;
+  cudaFree(L.f64.inv);
+  cudaFree(L.f32.inv);
+  L.f64.inv = nullptr;
+  L.f32.inv = nullptr;
 }
 
 bool check_prec(int prec) { return prec == NC_FP64 || prec == NC_FP32; }
@@ -159,6 +163,8 @@ void nc_destroy(nc_ctx* ctx) {
   cudaFree(ctx->kry.y);
   for (auto& p : ctx->tmp64) cudaFree(p);
   for (auto& p : ctx->tmp32) cudaFree(p);
+  cudaFree(ctx->cjel);
+  if (ctx->cap) cudaStreamDestroy(ctx->cap);
   delete ctx;
 }
 

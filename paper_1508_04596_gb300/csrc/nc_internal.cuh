@@ -50,6 +50,7 @@ struct LevelBuf {
   double* Hd = nullptr;  // device scalars: Hessenberg (MAX_RESTART+1)^2, y, beta, norms
   int ks = 0;
   bool ext = false;    // x and gam point to caller/Newton arrays (level 0, FP64)
+  R* inv = nullptr;    // dense inverse of the level operator (coarsest level only)
 };
 
 struct Level {
@@ -84,6 +85,9 @@ struct nc_ctx {
   double* tmp64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // FP64 [5][Nn]
   float* tmp32[2] = {nullptr, nullptr};
   int ws_ks = 0;              // smoother workspace size allocated
+  double* cjel = nullptr;     // coarsest-level element Jacobians (40 x 40 per element)
+  long long cjel_elems = 0;
+  cudaStream_t cap = nullptr; // stream used to capture the V-cycle graph
   std::string err;
 };
 
@@ -152,5 +156,14 @@ void vmaxpy(long long n, int k, const R* X, long long ld, const double* coef, do
 template <typename R>
 void vscale_inv(long long n, const R* x, const double* nrm, R* y, cudaStream_t s);
 void dev_sqrt_store(const double* in, double* out, cudaStream_t s);
+
+// ---- coarsest-level direct solve (nc_coarse.cu)
+constexpr int COARSE_DENSE_MAX = 1000;  // largest coarsest level solved by a dense inverse
+int coarse_dense_dofs(const Level& L);
+template <typename R>
+nc_status coarse_setup(nc_ctx* ctx, Level& L, const R* x, const R* gam, const R* src, R** inv,
+                       cudaStream_t s);
+template <typename R>
+void coarse_apply(const Level& L, bool tr, const R* inv, const R* b, R* z, cudaStream_t s);
 
 }  // namespace nc

@@ -138,7 +138,10 @@ void vcycle(nc_ctx* ctx, int l, int nlev, bool tr, const nc_solve_opts& o, cudaS
   LevelBuf<R>& B = buf<R>(L);
   const long long n = 5 * L.d.Nn;
   if (l == nlev - 1) {
-    smooth<R>(ctx, l, tr, o.coarse_its, true, s);
+    if (B.inv)
+      coarse_apply<R>(L, tr, B.inv, B.b, B.z, s);
+    else
+      smooth<R>(ctx, l, tr, o.coarse_its, true, s);
     return;
   }
   smooth<R>(ctx, l, tr, o.smooth_its, true, s);
@@ -186,7 +189,7 @@ nc_status alloc_levels(nc_ctx* ctx, int nlev, const nc_solve_opts& o) {
 // level 0 is x, gamma themselves (FP64) or their FP32 casts; coarser levels take
 // the injected state and the mean design of the eight children; then diag(J).
 template <typename R>
-void linearize(nc_ctx* ctx, int nlev, const double* x, const double* gam, bool tr, cudaStream_t s) {
+nc_status linearize(nc_ctx* ctx, int nlev, const double* x, const double* gam, cudaStream_t s) {
   for (int l = 0; l < nlev; ++l) {
     Level& L = ctx->lv[l];
     LevelBuf<R>& B = buf<R>(L);
@@ -205,9 +208,16 @@ void linearize(nc_ctx* ctx, int nlev, const double* x, const double* gam, bool t
       op_coarsen_elem<R>(F.d, buf<R>(F).gam, L.d, B.gam, s);
     }
     // diag(J^T) = diag(J)
-    (void)tr;
     op_diag<R>(L.d, cst<R>(L), B.x, B.gam, B.src, B.diag, (R*)ctx->Y, s);
+    if (l == nlev - 1 && coarse_dense_dofs(L) <= COARSE_DENSE_MAX) {
+      const nc_status st = coarse_setup<R>(ctx, L, B.x, B.gam, B.src, &B.inv, s);
+      if (st != NC_OK) return st;
+    } else if (B.inv) {
+      cudaFree(B.inv);  // a previous solve used this level as the coarsest
+      B.inv = nullptr;
+    }
   }
+  return NC_OK;
 }
 
 void release_ext(nc_ctx* ctx) {
@@ -226,20 +236,64 @@ struct LinSolve {
   int nlev = 1;
 };
 
+// The V-cycle (level-0 b -> level-0 z) of one linear solve, captured once into a
+// CUDA graph: a cycle is hundreds of small kernels on the coarse levels, and
+// replaying the graph removes their per-launch host overhead.  If capture is
+// not possible the cycle is launched kernel by kernel.
+struct CycleGraph {
+  cudaGraphExec_t exec = nullptr;
+  ~CycleGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+void run_cycle(nc_ctx* ctx, const LinSolve& ls, const nc_solve_opts& o, cudaStream_t s) {
+  if (ls.mixed)
+    vcycle<float>(ctx, 0, ls.nlev, ls.tr, o, s);
+  else
+    vcycle<double>(ctx, 0, ls.nlev, ls.tr, o, s);
+}
+
+void capture_cycle(nc_ctx* ctx, const LinSolve& ls, const nc_solve_opts& o, CycleGraph& g) {
+  if (!ctx->cap && cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    ctx->cap = nullptr;
+    cudaGetLastError();
+    return;
+  }
+  if (cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  run_cycle(ctx, ls, o, ctx->cap);
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamEndCapture(ctx->cap, &graph) != cudaSuccess || !graph) {
+    cudaGetLastError();
+    return;
+  }
+  if (cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    g.exec = nullptr;
+  }
+  cudaGraphDestroy(graph);
+}
+
 // z = M^-1 v (one V-cycle in the chosen precision)
-void precond(nc_ctx* ctx, const LinSolve& ls, const nc_solve_opts& o, const double* v, double* z,
-             cudaStream_t s) {
+void precond(nc_ctx* ctx, const LinSolve& ls, const nc_solve_opts& o, const CycleGraph& g,
+             const double* v, double* z, cudaStream_t s) {
   Level& L = ctx->lv[0];
   const long long n = 5 * L.d.Nn;
-  if (ls.mixed) {
+  if (ls.mixed)
     vcast(n, v, L.f32.b, s);
-    vcycle<float>(ctx, 0, ls.nlev, ls.tr, o, s);
-    vcast(n, (const float*)L.f32.z, z, s);
-  } else {
+  else
     vcopy(n, v, L.f64.b, s);
-    vcycle<double>(ctx, 0, ls.nlev, ls.tr, o, s);
+  if (g.exec)
+    cudaGraphLaunch(g.exec, s);
+  else
+    run_cycle(ctx, ls, o, s);
+  if (ls.mixed)
+    vcast(n, (const float*)L.f32.z, z, s);
+  else
     vcopy(n, (const double*)L.f64.z, z, s);
-  }
 }
 
 // out = A v with the linear solve's operator (FP32 product in mixed mode)
@@ -281,12 +335,14 @@ nc_status fgmres(nc_ctx* ctx, const LinSolve& ls, const nc_solve_opts& o, const 
   double* V = ctx->kry.V;
   double* Z = ctx->kry.Z;
   double* hc = ctx->kry.hcol;
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hh(2 * (m + 2));
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hh(2 * (m + 2) + 1);
   vzero(n, x, s);
   double beta0;
   nc_status st = norm2(ctx, n, b, &beta0, s);
   if (st != NC_OK) return st;
   if (beta0 == 0.0) return NC_OK;
+  CycleGraph graph;
+  capture_cycle(ctx, ls, o, graph);
   bool first = true;
   int total = 0;
   while (total < o.max_lin) {
@@ -309,17 +365,17 @@ nc_status fgmres(nc_ctx* ctx, const LinSolve& ls, const nc_solve_opts& o, const 
       double* vj = V + j * n;
       double* zj = Z + j * n;
       double* w = V + (j + 1) * n;
-      precond(ctx, ls, o, vj, zj, s);
+      precond(ctx, ls, o, graph, vj, zj, s);
       apply_A(ctx, ls, zj, w, s);
       // classical Gram-Schmidt, twice
       vmdot(n, j + 1, (const double*)V, n, (const double*)w, hc, ctx->partial, s);
       vmaxpy(n, j + 1, (const double*)V, n, hc, 1.0, w, s);
       vmdot(n, j + 1, (const double*)V, n, (const double*)w, hc + (m + 2), ctx->partial, s);
       vmaxpy(n, j + 1, (const double*)V, n, hc + (m + 2), 1.0, w, s);
-      vmdot(n, 1, (const double*)w, 0, (const double*)w, ctx->dscal, ctx->partial, s);
-      if ((st = read_scalar(ctx, hc, hh.data(), 2 * (m + 2), s)) != NC_OK) return st;
-      double nw2;
-      if ((st = read_scalar(ctx, ctx->dscal, &nw2, 1, s)) != NC_OK) return st;
+      vmdot(n, 1, (const double*)w, 0, (const double*)w, hc + 2 * (m + 2), ctx->partial, s);
+      // one device-to-host read per iteration: both Gram-Schmidt columns and ||w||^2
+      if ((st = read_scalar(ctx, hc, hh.data(), 2 * (m + 2) + 1, s)) != NC_OK) return st;
+      const double nw2 = hh[2 * (m + 2)];
       if (!std::isfinite(nw2)) return set_err(ctx, NC_ERR_NAN, "non-finite value in FGMRES");
       const double nw = std::sqrt(std::fmax(nw2, 0.0));
       for (int i = 0; i <= j; ++i) H[i + (size_t)j * (m + 1)] = hh[i] + hh[(m + 2) + i];
@@ -397,7 +453,7 @@ nc_status prepare(nc_ctx* ctx, const nc_solve_opts& o, int nlev, bool mixed) {
     ctx->kry.m = o.restart;
   }
   if ((st = alloc(ctx, &ctx->kry.w, n)) != NC_OK ||
-      (st = alloc(ctx, &ctx->kry.hcol, 2LL * (MAX_RESTART + 2))) != NC_OK ||
+      (st = alloc(ctx, &ctx->kry.hcol, 2LL * (MAX_RESTART + 2) + 1)) != NC_OK ||
       (st = alloc(ctx, &ctx->kry.y, (long long)MAX_RESTART)) != NC_OK)
     return st;
   for (int i = 0; i < 6; ++i)
@@ -458,8 +514,8 @@ nc_status newton(nc_ctx* ctx, const double* gam, double* x, const nc_solve_opts&
       info->res_final = nr;
       return set_err(ctx, NC_ERR_MAXIT, "Newton reached max_newton");
     }
-    if (mixed) linearize<float>(ctx, nlev, x, gam, false, s);
-    else linearize<double>(ctx, nlev, x, gam, false, s);
+    st = mixed ? linearize<float>(ctx, nlev, x, gam, s) : linearize<double>(ctx, nlev, x, gam, s);
+    if (st != NC_OK) return st;
     // J d = R, the Newton step is -d
     int lits = 0;
     st = fgmres(ctx, ls, o, R, d, o.rtol_lin, &lits, s);
@@ -514,7 +570,7 @@ void nc_default_opts(nc_solve_opts* o) {
   o->max_lin = 200;
   o->restart = 30;
   o->mg_levels = 0;
-  o->smooth_its = 2;
+  o->smooth_its = 4;
   o->coarse_its = 30;
   o->mixed = 1;
   o->ramp_steps = 0;
@@ -594,8 +650,8 @@ nc_status nc_adjoint_solve(nc_ctx* ctx, const double* x, const double* gam, cons
     double nr = nb;
     while (st == NC_OK && nr > o.rtol_newton * nb && nr > 0.0) {
       if (k >= o.max_newton) { st = set_err(ctx, NC_ERR_MAXIT, "adjoint refinement limit"); break; }
-      if (mixed) linearize<float>(ctx, nlev, x, gam, true, s);
-      else linearize<double>(ctx, nlev, x, gam, true, s);
+      st = mixed ? linearize<float>(ctx, nlev, x, gam, s) : linearize<double>(ctx, nlev, x, gam, s);
+      if (st != NC_OK) break;
       int lits = 0;
       // inner relative tolerance: no tighter than needed for the outer target
       const double rt = std::fmax(o.rtol_lin, 0.5 * o.rtol_newton * nb / nr);
