@@ -484,9 +484,13 @@ double line_search_length(double n0, double nh, double n1) {
   return nh < n1 ? 0.5 : 1.0;
 }
 
-// Newton at the context's current Gr, from x (Dirichlet values already imposed).
+// Newton at the context's current Gr, from x (Dirichlet values already imposed),
+// until ||R|| <= max(rtol ||R_0||, atol).  With stall_fails, three consecutive
+// steps shorter than 0.1 that reduce ||R|| by less than 10 % count as a failure
+// (NC_ERR_DIVERGED), which lets the caller switch to ramping.
 nc_status newton(nc_ctx* ctx, const double* gam, double* x, const nc_solve_opts& o,
-                 nc_solve_info* info, cudaStream_t s) {
+                 nc_solve_info* info, cudaStream_t s, double rtol, double atol,
+                 bool stall_fails) {
   Level& L = ctx->lv[0];
   const long long n = 5 * L.d.Nn;
   const int nlev = n_levels(ctx, o);
@@ -509,7 +513,8 @@ nc_status newton(nc_ctx* ctx, const double* gam, double* x, const nc_solve_opts&
   };
   if (info->newton_its == 0) hist(r0);
   const LinSolve ls{false, mixed, nlev};
-  while (nr > o.rtol_newton * r0 && nr > 0.0) {
+  int stalls = 0;
+  while (nr > std::fmax(rtol * r0, atol) && nr > 0.0) {
     if (it >= o.max_newton) {
       info->res_final = nr;
       return set_err(ctx, NC_ERR_MAXIT, "Newton reached max_newton");
@@ -552,7 +557,12 @@ nc_status newton(nc_ctx* ctx, const double* gam, double* x, const nc_solve_opts&
       info->res_final = nr;
       return set_err(ctx, NC_ERR_DIVERGED, "Newton: no decrease of the residual norm");
     }
+    stalls = (lam <= 0.1 && nn > 0.9 * nr) ? stalls + 1 : 0;
     nr = nn;
+    if (stall_fails && stalls >= 3) {
+      info->res_final = nr;
+      return set_err(ctx, NC_ERR_DIVERGED, "Newton: damped steps stagnate");
+    }
   }
   info->res_final = nr;
   return NC_OK;
@@ -594,17 +604,21 @@ nc_status nc_newton_solve(nc_ctx* ctx, const double* gam, double* x, const nc_so
     op_impose<double>(L.d, x, s);
     // keep the start for a ramped retry
     if (o.ramp_steps > 0) vcopy(n, (const double*)x, ctx->tmp64[5], s);
-    st = newton(ctx, gam, x, o, &info, s);
+    st = newton(ctx, gam, x, o, &info, s, o.rtol_newton, 0.0, o.ramp_steps > 0);
     if (st != NC_OK && st != NC_ERR_ARG && st != NC_ERR_CUDA && st != NC_ERR_OOM &&
         o.ramp_steps > 0) {
-      // ramp the buoyancy: Gr / 10^steps, ..., Gr / 10, Gr, each from the last state
+      // Sec. 5.1: recover from a failed start by ramping the load.  Here the
+      // buoyancy is ramped: Gr / 10^steps, ..., Gr / 10 (each to 1e-4 of its own
+      // initial residual, the paper's Newton tolerance), then Gr to the requested
+      // tolerance relative to the initial residual of the original problem.
+      const double target = o.rtol_newton * info.res0;
       vcopy(n, (const double*)ctx->tmp64[5], x, s);
-      info.res0 = 0.0;
-      info.newton_its = 0;
       for (int k = o.ramp_steps; k >= 0; --k) {
         set_Gr(ctx, ctx->prm.Gr * std::pow(10.0, -k));
-        st = newton(ctx, gam, x, o, &info, s);
-        if (st != NC_OK && k == 0) break;
+        if (k > 0)
+          st = newton(ctx, gam, x, o, &info, s, std::fmax(o.rtol_newton, 1e-4), 0.0, false);
+        else
+          st = newton(ctx, gam, x, o, &info, s, 0.0, target, false);
         if (st != NC_OK && st != NC_ERR_MAXIT && st != NC_ERR_DIVERGED) break;
       }
       set_Gr(ctx, ctx->prm.Gr);

@@ -98,6 +98,20 @@ def design(name_or_cfg, seed=None):
     return gen(cfg["nx"], cfg["ny"], cfg["nz"], cfg["h"], s)
 
 
+def design_step(name_or_cfg, gam, seed, amp=0.02):
+    """A synthetic optimiser step: gamma + amp * (box-filtered U[-1,1] noise) inside
+    the design column, clipped to [0, 1] (the next design of an optimisation run,
+    whose state solve is warm-started from the current one)."""
+    cfg = WORKLOADS[name_or_cfg] if isinstance(name_or_cfg, str) else name_or_cfg
+    nx, ny, nz, h = cfg["nx"], cfg["ny"], cfg["nz"], cfg["h"]
+    rng = np.random.default_rng(seed)
+    d = box_filter3(rng.uniform(-1.0, 1.0, size=(nz, ny, nx))).ravel()
+    col = design_column(nx, ny, nz, h)
+    out = np.array(gam, dtype=float, copy=True)
+    out[col] = np.clip(out[col] + amp * d[col], 0.0, 1.0)
+    return out
+
+
 def random_state(nx, ny, nz, seed, scale=(1.0, 1.0, 1.0, 1.0, 1.0)):
     """Random nodal state, [5, Nn], N(0, scale_f^2) per field (Dirichlet values
     are imposed by whoever consumes it)."""
