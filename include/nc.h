@@ -176,7 +176,8 @@ nc_status nc_sensitivity(nc_ctx* ctx, const double* x, const double* gamma,
 nc_status nc_jvp_static(const nc_params* prm, const nc_bcs* bcs, const void* x,
                         const void* gamma, const void* v, void* Jv, int prec, void* stream);
 
-/* Solver options.  rtol_newton: stop when ||R|| <= rtol_newton ||R_0|| (Sec. 5.1);
+/* Solver options.  rtol_newton: stop when ||R|| <= max(rtol_newton ||R_0||,
+ * atol_newton) (Sec. 5.1 uses a relative tolerance);
  * rtol_lin: FGMRES relative tolerance per linear solve (Sec. 5.2); max_newton,
  * max_lin (total FGMRES iterations per linear solve), restart (FGMRES restart,
  * <= 64); mg_levels: multigrid levels to use (0 = all); smooth_its: Jacobi-GMRES
@@ -193,6 +194,7 @@ typedef struct {
   int mg_levels, smooth_its, coarse_its;
   int mixed;
   int ramp_steps;
+  double atol_newton;  /* also stop when ||R|| <= atol_newton (default 0) */
 } nc_solve_opts;
 
 /* Per-solve report (Sec. 6.2 reports Newton and linear iteration counts). */

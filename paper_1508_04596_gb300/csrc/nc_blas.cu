@@ -122,13 +122,66 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot_partial(long long n, int k
 }
 
 __global__ void __launch_bounds__(RED_THREADS) k_mdot_final(int nb, const double* partial,
-                                                            double* out) {
+                                                            double* out, int take_sqrt) {
   __shared__ double sh[RED_THREADS / 32];
   const int i = blockIdx.x;
   double acc = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += partial[i * nb + b];
   const double s = block_sum(acc, sh);
-  if (threadIdx.x == 0) out[i] = s;
+  if (threadIdx.x == 0) out[i] = take_sqrt ? sqrt(fmax(s, 0.0)) : s;
+}
+
+// y -= sum_i coef[i] X_i, and partial[b] = sum of y^2 over block b's range
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) k_maxpy_norm(long long n, int k,
+                                                            const R* __restrict__ X, long long ld,
+                                                            const double* __restrict__ coef,
+                                                            R* __restrict__ y, double* partial) {
+  __shared__ R c[MAX_RESTART + 1];
+  __shared__ R sh[RED_THREADS / 32];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) c[i] = R(coef[i]);
+  __syncthreads();
+  R acc2 = R(0);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    R acc = y[t];
+    for (int i = 0; i < k; ++i) acc -= c[i] * X[i * ld + t];
+    y[t] = acc;
+    acc2 += acc * acc;
+  }
+  const R s = block_sum(acc2, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = double(s);
+}
+
+// v = x / *nrm (zero on a vanishing or non-finite norm) and t = v / d
+template <typename R>
+__global__ void k_scale_div(long long n, const R* __restrict__ x, const double* __restrict__ nrm,
+                            const R* __restrict__ d, R* __restrict__ v, R* __restrict__ t) {
+  const double nv = *nrm;
+  const R s = (nv > 0.0 && nv < 1e300) ? R(1.0 / nv) : R(0);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const R a = x[i] * s;
+    v[i] = a;
+    t[i] = a / d[i];
+  }
+}
+
+// z (+)= (sum_i y[i] X_i) / d
+template <typename R>
+__global__ void k_combine_div(long long n, int k, const R* __restrict__ X, long long ld,
+                              const double* __restrict__ y, const R* __restrict__ d, R* z,
+                              int accumulate) {
+  __shared__ R c[MAX_RESTART + 1];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) c[i] = R(y[i]);
+  __syncthreads();
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    R acc = R(0);
+    for (int i = 0; i < k; ++i) acc += c[i] * X[i * ld + t];
+    acc /= d[t];
+    z[t] = accumulate ? z[t] + acc : acc;
+  }
 }
 
 template <typename R>
@@ -198,7 +251,30 @@ void vmdot(long long n, int k, const R* X, long long ld, const R* y, double* out
            cudaStream_t s) {
   const int nb = red_blocks(n);
   k_mdot_partial<R><<<nb, RED_THREADS, 0, s>>>(n, k, X, ld, y, partial);
-  k_mdot_final<<<k, RED_THREADS, 0, s>>>(nb, partial, out);
+  k_mdot_final<<<k, RED_THREADS, 0, s>>>(nb, partial, out, 0);
+}
+template <typename R>
+void vnorm(long long n, const R* x, double* out, double* partial, cudaStream_t s) {
+  const int nb = red_blocks(n);
+  k_mdot_partial<R><<<nb, RED_THREADS, 0, s>>>(n, 1, x, 0, x, partial);
+  k_mdot_final<<<1, RED_THREADS, 0, s>>>(nb, partial, out, 1);
+}
+template <typename R>
+void vmaxpy_norm(long long n, int k, const R* X, long long ld, const double* coef, R* y,
+                 double* out_norm, double* partial, cudaStream_t s) {
+  const int nb = red_blocks(n);
+  k_maxpy_norm<R><<<nb, RED_THREADS, 0, s>>>(n, k, X, ld, coef, y, partial);
+  k_mdot_final<<<1, RED_THREADS, 0, s>>>(nb, partial, out_norm, 1);
+}
+template <typename R>
+void vscale_div(long long n, const R* x, const double* nrm, const R* d, R* v, R* t,
+                cudaStream_t s) {
+  k_scale_div<R><<<vblocks(n), VT, 0, s>>>(n, x, nrm, d, v, t);
+}
+template <typename R>
+void vcombine_div(long long n, int k, const R* X, long long ld, const double* y, const R* d, R* z,
+                  bool accumulate, cudaStream_t s) {
+  k_combine_div<R><<<vblocks(n), VT, 0, s>>>(n, k, X, ld, y, d, z, accumulate ? 1 : 0);
 }
 template <typename R>
 void vmaxpy(long long n, int k, const R* X, long long ld, const double* coef, double sign, R* y,
@@ -227,7 +303,14 @@ template void vcast<double, float>(long long, const float*, double*, cudaStream_
                          cudaStream_t);                                                        \
   template void vmaxpy<R>(long long, int, const R*, long long, const double*, double, R*,      \
                           cudaStream_t);                                                       \
-  template void vscale_inv<R>(long long, const R*, const double*, R*, cudaStream_t);
+  template void vscale_inv<R>(long long, const R*, const double*, R*, cudaStream_t);            \
+  template void vnorm<R>(long long, const R*, double*, double*, cudaStream_t);                 \
+  template void vmaxpy_norm<R>(long long, int, const R*, long long, const double*, R*, double*, \
+                               double*, cudaStream_t);                                         \
+  template void vscale_div<R>(long long, const R*, const double*, const R*, R*, R*,           \
+                              cudaStream_t);                                                   \
+  template void vcombine_div<R>(long long, int, const R*, long long, const double*, const R*,  \
+                                R*, bool, cudaStream_t);
 NC_INST(double)
 NC_INST(float)
 #undef NC_INST

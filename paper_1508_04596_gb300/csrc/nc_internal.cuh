@@ -156,6 +156,21 @@ void vmaxpy(long long n, int k, const R* X, long long ld, const double* coef, do
 template <typename R>
 void vscale_inv(long long n, const R* x, const double* nrm, R* y, cudaStream_t s);
 void dev_sqrt_store(const double* in, double* out, cudaStream_t s);
+// *out = ||x||_2
+template <typename R>
+void vnorm(long long n, const R* x, double* out, double* partial, cudaStream_t s);
+// y -= sum_i coef[i] X_i, then *out = ||y||_2
+template <typename R>
+void vmaxpy_norm(long long n, int k, const R* X, long long ld, const double* coef, R* y,
+                 double* out_norm, double* partial, cudaStream_t s);
+// v = x / *nrm (0 if the norm vanishes), t = v / d
+template <typename R>
+void vscale_div(long long n, const R* x, const double* nrm, const R* d, R* v, R* t,
+                cudaStream_t s);
+// z = (sum_i y[i] X_i) / d, or z += ... with accumulate
+template <typename R>
+void vcombine_div(long long n, int k, const R* X, long long ld, const double* y, const R* d, R* z,
+                  bool accumulate, cudaStream_t s);
 
 // ---- coarsest-level direct solve (nc_coarse.cu)
 constexpr int COARSE_DENSE_MAX = 1000;  // largest coarsest level solved by a dense inverse

@@ -28,9 +28,9 @@ using namespace nc;
 namespace {
 
 constexpr int LDH = MAX_RESTART + 1;            // leading dimension of device Hessenbergs
-constexpr int HD_SIZE = LDH * LDH + 2 * LDH + 8;  // H, y, g, scalars
-constexpr int HD_Y = LDH * LDH;
-constexpr int HD_BETA = LDH * LDH + 2 * LDH;      // scalar slots
+constexpr int HD_Y = LDH * LDH;                   // y, then g, then the rotations
+constexpr int HD_BETA = HD_Y + 4 * LDH;           // scalar slots
+constexpr int HD_SIZE = HD_BETA + 8;
 constexpr int HD_TMP = HD_BETA + 1;
 
 template <typename R> LevelBuf<R>& buf(Level& L);
@@ -47,36 +47,40 @@ nc_status alloc(nc_ctx* ctx, R** p, long long n) {
 }
 
 // Least squares  min || beta e1 - H y ||  for a (k+1) x k upper Hessenberg H
-// (column-major, leading dimension LDH) by Givens rotations; y -> Hd[HD_Y..].
-// A vanishing pivot (exhausted Krylov space) gives the corresponding y = 0.
+// (column-major, leading dimension LDH, in Hd) by Givens rotations, in place;
+// y -> Hd[HD_Y..].  A vanishing pivot (exhausted Krylov space) gives y = 0 there.
 __global__ void k_small_ls(double* Hd, int k) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double R[LDH * LDH];
-  double g[LDH + 1];
-  for (int j = 0; j < k; ++j)
-    for (int i = 0; i <= j + 1; ++i) R[i + j * LDH] = Hd[i + j * LDH];
+  double* g = Hd + HD_Y + LDH;  // right-hand side, k + 1 entries
   const double beta = Hd[HD_BETA];
   for (int i = 0; i <= k; ++i) g[i] = 0.0;
   g[0] = (beta > 0.0 && beta < 1e300) ? beta : 0.0;
+  double rmax = 0.0;
   for (int j = 0; j < k; ++j) {
-    const double a = R[j + j * LDH], b = R[j + 1 + j * LDH];
+    double* hj = Hd + j * LDH;
+    // apply the previous rotations (kept after g) to column j
+    for (int q = 0; q < j; ++q) {
+      const double c = Hd[HD_Y + 2 * LDH + 2 * q], s = Hd[HD_Y + 2 * LDH + 2 * q + 1];
+      const double t1 = hj[q], t2 = hj[q + 1];
+      hj[q] = c * t1 + s * t2;
+      hj[q + 1] = -s * t1 + c * t2;
+    }
+    const double a = hj[j], b = hj[j + 1];
     const double r = hypot(a, b);
     const double c = r > 0.0 ? a / r : 1.0, s = r > 0.0 ? b / r : 0.0;
-    for (int q = j; q < k; ++q) {
-      const double t1 = R[j + q * LDH], t2 = R[j + 1 + q * LDH];
-      R[j + q * LDH] = c * t1 + s * t2;
-      R[j + 1 + q * LDH] = -s * t1 + c * t2;
-    }
+    Hd[HD_Y + 2 * LDH + 2 * j] = c;
+    Hd[HD_Y + 2 * LDH + 2 * j + 1] = s;
+    hj[j] = r;
+    hj[j + 1] = 0.0;
     const double g1 = g[j], g2 = g[j + 1];
     g[j] = c * g1 + s * g2;
     g[j + 1] = -s * g1 + c * g2;
+    rmax = fmax(rmax, fabs(r));
   }
-  double rmax = 0.0;
-  for (int j = 0; j < k; ++j) rmax = fmax(rmax, fabs(R[j + j * LDH]));
   for (int j = k - 1; j >= 0; --j) {
     double acc = g[j];
-    for (int q = j + 1; q < k; ++q) acc -= R[j + q * LDH] * Hd[HD_Y + q];
-    const double d = R[j + j * LDH];
+    for (int q = j + 1; q < k; ++q) acc -= Hd[j + q * LDH] * Hd[HD_Y + q];
+    const double d = Hd[j + j * LDH];
     Hd[HD_Y + j] = (fabs(d) > 1e-14 * rmax && isfinite(acc)) ? acc / d : 0.0;
   }
 }
@@ -93,7 +97,9 @@ void level_apply(nc_ctx* ctx, int l, bool tr, const R* v, R* out, cudaStream_t s
 }
 
 // Right Jacobi-preconditioned GMRES(k) on level l:  z += D^-1 V y  approximately
-// solving A z = b.  With zero_init the initial guess is 0.
+// solving A z = b.  With zero_init the initial guess is 0.  Per Arnoldi step:
+// the operator on t = v_j / D, one multi-dot, one update-and-norm, and one
+// kernel that normalises v_{j+1} and forms the next t.
 template <typename R>
 void smooth(nc_ctx* ctx, int l, bool tr, int k, bool zero_init, cudaStream_t s) {
   Level& L = ctx->lv[l];
@@ -101,35 +107,25 @@ void smooth(nc_ctx* ctx, int l, bool tr, int k, bool zero_init, cudaStream_t s) 
   const long long n = 5 * L.d.Nn;
   R* V = B.V;
   double* Hd = B.Hd;
-  // V0 = b - A z
-  if (zero_init) {
-    vzero(n, B.z, s);
-    vcopy(n, (const R*)B.b, V, s);
-  } else {
+  const R* r0 = B.b;
+  if (!zero_init) {
     level_apply<R>(ctx, l, tr, B.z, B.t, s);
-    vwaxpy(n, (const R*)B.b, R(-1), (const R*)B.t, V, s);
+    vwaxpy(n, (const R*)B.b, R(-1), (const R*)B.t, B.r, s);
+    r0 = B.r;
   }
-  vmdot(n, 1, V, 0, V, Hd + HD_TMP, ctx->partial, s);
-  dev_sqrt_store(Hd + HD_TMP, Hd + HD_BETA, s);
-  vscale_inv(n, (const R*)V, Hd + HD_BETA, V, s);
+  vnorm(n, r0, Hd + HD_BETA, ctx->partial, s);
+  vscale_div(n, r0, Hd + HD_BETA, (const R*)B.diag, V, B.t, s);
   for (int j = 0; j < k; ++j) {
-    R* vj = V + j * n;
     R* w = V + (j + 1) * n;
-    vdiv(n, (const R*)vj, (const R*)B.diag, B.t, s);
     level_apply<R>(ctx, l, tr, B.t, w, s);
     double* hcol = Hd + j * LDH;
     vmdot(n, j + 1, (const R*)V, n, (const R*)w, hcol, ctx->partial, s);
-    vmaxpy(n, j + 1, (const R*)V, n, hcol, 1.0, w, s);
-    vmdot(n, 1, (const R*)w, 0, (const R*)w, Hd + HD_TMP, ctx->partial, s);
-    dev_sqrt_store(Hd + HD_TMP, hcol + j + 1, s);
-    vscale_inv(n, (const R*)w, hcol + j + 1, w, s);
+    vmaxpy_norm(n, j + 1, (const R*)V, n, hcol, w, hcol + j + 1, ctx->partial, s);
+    if (j + 1 < k) vscale_div(n, (const R*)w, hcol + j + 1, (const R*)B.diag, w, B.t, s);
   }
   k_small_ls<<<1, 1, 0, s>>>(Hd, k);
-  // z += D^-1 (V y)
-  vzero(n, B.t, s);
-  vmaxpy(n, k, (const R*)V, n, Hd + HD_Y, -1.0, B.t, s);
-  vdiv(n, (const R*)B.t, (const R*)B.diag, B.t, s);
-  vaxpy(n, R(1), (const R*)B.t, B.z, s);
+  // z (+)= D^-1 (V y); the last basis vector is not needed
+  vcombine_div(n, k, (const R*)V, n, Hd + HD_Y, (const R*)B.diag, B.z, !zero_init, s);
 }
 
 template <typename R>
@@ -438,7 +434,8 @@ nc_status prepare(nc_ctx* ctx, const nc_solve_opts& o, int nlev, bool mixed) {
   nc_status st;
   if (o.restart < 1 || o.restart > MAX_RESTART || o.smooth_its < 1 ||
       o.smooth_its > MAX_RESTART || o.coarse_its < 1 || o.coarse_its > MAX_RESTART ||
-      o.max_lin < 1 || o.max_newton < 0 || !(o.rtol_lin > 0.0) || !(o.rtol_newton >= 0.0))
+      o.max_lin < 1 || o.max_newton < 0 || !(o.rtol_lin > 0.0) || !(o.rtol_newton >= 0.0) ||
+      !(o.atol_newton >= 0.0))
     return set_err(ctx, NC_ERR_ARG, "invalid solver options");
   if (ctx->kry.m < o.restart) {
     cudaFree(ctx->kry.V);
@@ -584,6 +581,7 @@ void nc_default_opts(nc_solve_opts* o) {
   o->coarse_its = 30;
   o->mixed = 1;
   o->ramp_steps = 0;
+  o->atol_newton = 0.0;
 }
 
 nc_status nc_newton_solve(nc_ctx* ctx, const double* gam, double* x, const nc_solve_opts* opts,
@@ -604,14 +602,14 @@ nc_status nc_newton_solve(nc_ctx* ctx, const double* gam, double* x, const nc_so
     op_impose<double>(L.d, x, s);
     // keep the start for a ramped retry
     if (o.ramp_steps > 0) vcopy(n, (const double*)x, ctx->tmp64[5], s);
-    st = newton(ctx, gam, x, o, &info, s, o.rtol_newton, 0.0, o.ramp_steps > 0);
+    st = newton(ctx, gam, x, o, &info, s, o.rtol_newton, o.atol_newton, o.ramp_steps > 0);
     if (st != NC_OK && st != NC_ERR_ARG && st != NC_ERR_CUDA && st != NC_ERR_OOM &&
         o.ramp_steps > 0) {
       // Sec. 5.1: recover from a failed start by ramping the load.  Here the
       // buoyancy is ramped: Gr / 10^steps, ..., Gr / 10 (each to 1e-4 of its own
       // initial residual, the paper's Newton tolerance), then Gr to the requested
       // tolerance relative to the initial residual of the original problem.
-      const double target = o.rtol_newton * info.res0;
+      const double target = std::fmax(o.rtol_newton * info.res0, o.atol_newton);
       vcopy(n, (const double*)ctx->tmp64[5], x, s);
       for (int k = o.ramp_steps; k >= 0; --k) {
         set_Gr(ctx, ctx->prm.Gr * std::pow(10.0, -k));

@@ -49,7 +49,8 @@ class SolveOpts(ctypes.Structure):
                 ("max_newton", ctypes.c_int), ("max_lin", ctypes.c_int),
                 ("restart", ctypes.c_int), ("mg_levels", ctypes.c_int),
                 ("smooth_its", ctypes.c_int), ("coarse_its", ctypes.c_int),
-                ("mixed", ctypes.c_int), ("ramp_steps", ctypes.c_int)]
+                ("mixed", ctypes.c_int), ("ramp_steps", ctypes.c_int),
+                ("atol_newton", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
