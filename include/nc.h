@@ -140,10 +140,12 @@ nc_status nc_jtvp(nc_ctx* ctx, const void* x, const void* gamma, const void* w, 
 nc_status nc_diag(nc_ctx* ctx, const void* x, const void* gamma, void* d, int prec,
                   void* stream);
 
-/* Objective: mean temperature of the bottom patch, Phi = (1/|Gamma_p|) int T dA
- * (the patch analogue of the thermal compliance of Sec. 3.2).  FP64 only.
- * phi_host receives Phi (the call synchronises the stream); dphidx, if not NULL,
- * receives dPhi/dx as [5][Nn]. */
+/* Objective.  With patch_mode NC_PATCH_NONE and an element source set
+ * (nc_set_source): the thermal compliance of Sec. 3.2, f = int_omega s T dV.
+ * Otherwise: the mean temperature of the bottom patch,
+ * Phi = (1/|Gamma_p|) int T dA (the patch analogue of the same objective).
+ * FP64 only.  phi_host receives the value (the call synchronises the stream);
+ * dphidx, if not NULL, receives the gradient with respect to x as [5][Nn]. */
 nc_status nc_objective(nc_ctx* ctx, const double* x, double* phi_host, double* dphidx,
                        void* stream);
 
@@ -185,9 +187,10 @@ nc_status nc_jvp_static(const nc_params* prm, const nc_bcs* bcs, const void* x,
  * the coarsest level when it has more than 1000 unknowns (smaller coarsest levels
  * are solved with a dense inverse formed once per linearisation); mixed: 1 = Jacobian products, smoother and coarse levels
  * in FP32 inside FP64 Newton / refinement, 0 = everything FP64; ramp_steps: on
- * Newton failure from the given start, retry with the buoyancy (Gr) ramped up
- * in this many geometric steps (0 = no ramping; the paper ramps the heat load,
- * Sec. 5.1). */
+ * Newton failure (or stagnation) from the given start, continue in the buoyancy
+ * from Gr / 10^ramp_steps up to Gr, each stage warm-started from the last, with
+ * the step in log Gr halved after a failed stage and grown after a converged
+ * one (0 = no ramping; the paper ramps the heat load, Sec. 5.1). */
 typedef struct {
   double rtol_newton, rtol_lin;
   int max_newton, max_lin, restart;

@@ -7,9 +7,11 @@
   raised to at least 0.05; otherwise the sampled length (1/2 or 1) with the
   smaller norm, the longer one on a tie.  Linear systems are solved directly
   (sparse LU), so the linear solve is exact.
-* Objective (reading of Sec. 3.2's thermal compliance for a heated patch):
-  Phi = (1/|Gamma_p|) int_{Gamma_p} T dA, the mean temperature of the bottom
-  patch, integrated with 2x2 Gauss per face (exact for bilinear T).
+* Objective.  With a heat source and no patch, the thermal compliance of
+  Sec. 3.2, f = int_omega s T dV, with s element-constant and T trilinear:
+  int_e N_a dV = h^3/8 exactly.  With a patch (reading of the same objective
+  for a heated patch): Phi = (1/|Gamma_p|) int_{Gamma_p} T dA, the mean
+  temperature of the bottom patch, 2x2 Gauss per face (exact for bilinear T).
 * Adjoint, Sec. 3.2: J^T lambda = -dPhi/dx with J = blockdiag(J_II, I).
 * Sensitivities: dPhi/dgamma_e = dPhi/dgamma_e|explicit (zero here)
   + lambda^T dR/dgamma_e, the element rows of Dirichlet unknowns excluded.
@@ -18,7 +20,7 @@ import numpy as np
 import scipy.sparse.linalg as spla
 
 from .assemble import gather
-from .grid import NF, patch_faces
+from .grid import NF, PATCH_NONE, patch_faces
 
 
 def line_search_length(n0, nh, n1):
@@ -65,10 +67,16 @@ def newton(prob, gam, x0, rtol=1e-10, atol=0.0, maxit=50, linsolve=None, history
 
 
 def objective(prob, bc, x):
-    """Mean patch temperature and its gradient dPhi/dx ([5, Nn])."""
+    """Objective and its gradient dPhi/dx ([5, Nn]): thermal compliance when the
+    patch mode is none and a source is present, else the mean patch temperature."""
     g = prob.g
-    faces = patch_faces(g, bc)
     dphi = np.zeros((NF, g.Nn))
+    if bc.patch_mode == PATCH_NONE and np.any(prob.se != 0.0):
+        w = prob.se * g.h ** 3 / 8.0
+        for a in range(8):
+            np.add.at(dphi[4], prob.conn[:, a], w)
+        return float(np.sum(dphi * x)), dphi
+    faces = patch_faces(g, bc)
     if faces.size == 0:
         return 0.0, dphi
     area = faces.size * g.h * g.h

@@ -345,8 +345,11 @@ nc_status nc_objective(nc_ctx* ctx, const double* x, double* phi_host, double* d
     if (!ctx->tmp64[3] && (st = dev_alloc(ctx, &ctx->tmp64[3], 5 * L.d.Nn)) != NC_OK) return st;
     g = ctx->tmp64[3];
   }
-  op_objective_grad(L.d, g, s);
-  // Phi = <dPhi/dx, x> (the objective is linear in T)
+  if (L.d.patch_mode == NC_PATCH_NONE && ctx->src64)
+    op_source_grad(L.d, ctx->src64, g, s);  // thermal compliance (Sec. 3.2)
+  else
+    op_objective_grad(L.d, g, s);  // mean patch temperature
+  // Phi = <dPhi/dx, x> (both objectives are linear in T)
   vmdot(5 * L.d.Nn, 1, g, 0, x, ctx->dscal, ctx->partial, s);
   if ((st = cuda_check(ctx, cudaMemcpyAsync(phi_host, ctx->dscal, sizeof(double),
                                             cudaMemcpyDeviceToHost, s), "nc_objective")) != NC_OK)

@@ -113,6 +113,7 @@ void op_impose(const LevelDev& d, R* x, cudaStream_t s);
 template <typename R>
 void op_mask(const LevelDev& d, R* x, cudaStream_t s);  // zero Dirichlet entries
 void op_objective_grad(const LevelDev& d, double* dphidx, cudaStream_t s);
+void op_source_grad(const LevelDev& d, const double* src, double* dphidx, cudaStream_t s);
 double patch_area(const LevelDev& d);
 
 // ---- transfers

@@ -186,6 +186,25 @@ __global__ void k_objective_grad(LevelDev d, double* g, double inv_area) {
   g[4 * d.Nn + n] = cnt * d.h * d.h * 0.25 * inv_area;
 }
 
+// Gradient of the thermal compliance f = int s T dV: T rows get
+// sum over the node's elements of s_e h^3 / 8 (int_e N_a dV = h^3/8), in a fixed
+// element order.
+__global__ void k_source_grad(LevelDev d, const double* __restrict__ src, double* g) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= d.Nn) return;
+  const int i = (int)(n % (d.nx + 1));
+  const long long t = n / (d.nx + 1);
+  const int j = (int)(t % (d.ny + 1));
+  const int k = (int)(t / (d.ny + 1));
+  double acc = 0.0;
+  for (int a = 0; a < 8; ++a) {
+    const int ie = i - (a & 1), je = j - ((a >> 1) & 1), ke = k - ((a >> 2) & 1);
+    if (ie < 0 || je < 0 || ke < 0 || ie >= d.nx || je >= d.ny || ke >= d.nz) continue;
+    acc += src[ie + (long long)d.nx * (je + (long long)d.ny * ke)];
+  }
+  g[4 * d.Nn + n] = acc * d.h * d.h * d.h * 0.125;
+}
+
 // ---- transfers between a fine level and the next coarser one (factor 2)
 // 1-D Q1 prolongation weight of coarse node I for fine node i: 1 if i == 2I,
 // 1/2 if |i - 2I| == 1.
@@ -332,6 +351,11 @@ void op_mask(const LevelDev& d, R* x, cudaStream_t s) {
 double patch_area(const LevelDev& d) {
   if (d.pi1 <= d.pi0 || d.pj1 <= d.pj0) return 0.0;
   return (double)(d.pi1 - d.pi0) * (double)(d.pj1 - d.pj0) * d.h * d.h;
+}
+
+void op_source_grad(const LevelDev& d, const double* src, double* g, cudaStream_t s) {
+  cudaMemsetAsync(g, 0, sizeof(double) * 5 * d.Nn, s);
+  k_source_grad<<<nblocks(d.Nn, NODE_THREADS), NODE_THREADS, 0, s>>>(d, src, g);
 }
 
 void op_objective_grad(const LevelDev& d, double* g, cudaStream_t s) {

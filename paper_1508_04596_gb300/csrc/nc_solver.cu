@@ -604,20 +604,49 @@ nc_status nc_newton_solve(nc_ctx* ctx, const double* gam, double* x, const nc_so
     if (o.ramp_steps > 0) vcopy(n, (const double*)x, ctx->tmp64[5], s);
     st = newton(ctx, gam, x, o, &info, s, o.rtol_newton, o.atol_newton, o.ramp_steps > 0);
     if (st != NC_OK && st != NC_ERR_ARG && st != NC_ERR_CUDA && st != NC_ERR_OOM &&
-        o.ramp_steps > 0) {
+        o.ramp_steps > 0 && ctx->prm.Gr > 0.0) {
       // Sec. 5.1: recover from a failed start by ramping the load.  Here the
-      // buoyancy is ramped: Gr / 10^steps, ..., Gr / 10 (each to 1e-4 of its own
-      // initial residual, the paper's Newton tolerance), then Gr to the requested
+      // buoyancy is continued in log Gr from Gr / 10^steps: every stage starts
+      // from the last converged state and is solved to 1e-4 of its own initial
+      // residual (the paper's Newton tolerance); a stage that fails (or stalls)
+      // is retried with half the step, a stage that converges lets the step grow
+      // by half.  The last stage, at Gr itself, is solved to the requested
       // tolerance relative to the initial residual of the original problem.
       const double target = std::fmax(o.rtol_newton * info.res0, o.atol_newton);
-      vcopy(n, (const double*)ctx->tmp64[5], x, s);
-      for (int k = o.ramp_steps; k >= 0; --k) {
-        set_Gr(ctx, ctx->prm.Gr * std::pow(10.0, -k));
-        if (k > 0)
-          st = newton(ctx, gam, x, o, &info, s, std::fmax(o.rtol_newton, 1e-4), 0.0, false);
-        else
-          st = newton(ctx, gam, x, o, &info, s, 0.0, target, false);
-        if (st != NC_OK && st != NC_ERR_MAXIT && st != NC_ERR_DIVERGED) break;
+      const double stage_rtol = std::fmax(o.rtol_newton, 1e-4);
+      double* xlast = ctx->tmp64[5];  // the start, then the last converged stage
+      const double lg_t = std::log10(ctx->prm.Gr);
+      double lg = lg_t - o.ramp_steps;
+      bool have = false;
+      for (int tries = 0; tries < 4 && !have; ++tries, lg -= 1.0) {
+        set_Gr(ctx, std::pow(10.0, lg));
+        vcopy(n, (const double*)xlast, x, s);
+        st = newton(ctx, gam, x, o, &info, s, stage_rtol, 0.0, true);
+        have = st == NC_OK;
+        if (!have && st != NC_ERR_MAXIT && st != NC_ERR_DIVERGED) break;
+      }
+      if (have) {
+        lg += 1.0;  // undo the loop's last decrement
+        vcopy(n, (const double*)x, xlast, s);
+        double step = 1.0;
+        int halvings = 0;
+        while (lg < lg_t - 1e-12) {
+          const double lg_try = std::fmin(lg + step, lg_t);
+          const bool last = lg_try >= lg_t - 1e-12;
+          set_Gr(ctx, last ? ctx->prm.Gr : std::pow(10.0, lg_try));
+          vcopy(n, (const double*)xlast, x, s);
+          st = last ? newton(ctx, gam, x, o, &info, s, 0.0, target, true)
+                    : newton(ctx, gam, x, o, &info, s, stage_rtol, 0.0, true);
+          if (st == NC_OK) {
+            lg = lg_try;
+            vcopy(n, (const double*)x, xlast, s);
+            step *= 1.5;
+          } else if ((st == NC_ERR_MAXIT || st == NC_ERR_DIVERGED) && ++halvings <= 8) {
+            step *= 0.5;
+          } else {
+            break;
+          }
+        }
       }
       set_Gr(ctx, ctx->prm.Gr);
     }

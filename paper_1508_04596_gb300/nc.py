@@ -126,6 +126,21 @@ def cavity_bcs(patch_mode=PATCH_DIRICHLET, patch_val=1.0, patch=(1 / 3, 2 / 3, 1
     return b
 
 
+def quarter_bcs(nx, ny, nz):
+    """The paper's quarter of a closed cavity (Sec. 6.1): symmetry planes on the
+    +x and +y faces, no-slip elsewhere, cold (T = 0) outer vertical walls and
+    top, insulated bottom; the pressure is pinned at the top outer corner node."""
+    b = BCs()
+    b.vel_bc[:] = [VEL_NOSLIP, VEL_SYMMETRY, VEL_NOSLIP, VEL_SYMMETRY, VEL_NOSLIP, VEL_NOSLIP]
+    b.T_bc[:] = [T_DIRICHLET, T_ADIABATIC, T_DIRICHLET, T_ADIABATIC, T_ADIABATIC, T_DIRICHLET]
+    b.T_val[:] = [0.0] * 6
+    b.patch[:] = [0.0, 0.0, 0.0, 0.0]
+    b.patch_mode = PATCH_NONE
+    b.patch_val = 0.0
+    b.p_pin = (nx + 1) * (ny + 1) * nz  # node (0, 0, nz)
+    return b
+
+
 def make_params(nx, ny, nz, h, Gr, Pr, alpha_max=1e4, q_alpha=1.0, q_f=1.0, Ck=0.1,
                 g_dir=(0.0, 0.0, -1.0)):
     p = Params()
@@ -160,9 +175,13 @@ class Problem:
     def from_workload(cls, name, **over):
         cfg = dict(synth.WORKLOADS[name])
         cfg.update(over)
-        mat = dict(synth.MATERIAL)
+        mat = synth.material(cfg)
         mat.update({k: over[k] for k in ("alpha_max", "q_alpha", "q_f", "Ck") if k in over})
         p = make_params(cfg["nx"], cfg["ny"], cfg["nz"], cfg["h"], cfg["Gr"], cfg["Pr"], **mat)
+        if cfg.get("bcs") == "quarter":
+            prob = cls(p, quarter_bcs(cfg["nx"], cfg["ny"], cfg["nz"]))
+            prob.set_source(torch.tensor(synth.source(cfg), dtype=torch.float64, device="cuda"))
+            return prob
         mode = PATCH_FLUX if cfg["patch"] == "flux" else PATCH_DIRICHLET
         return cls(p, cavity_bcs(mode, 1.0))
 

@@ -13,6 +13,8 @@ available, so design fields are generated:
     0.03125 L) in the design column with a linear solid-to-fluid ramp over two
     elements, seeded noise of amplitude 0.05, clamped to [0,1];
     the solid density rho is converted to the paper's gamma = 1 - rho.
+  * ``quarter``: the paper's quarter cavity (solid source block, design domain
+    at 1 - v_f with small seeded noise, fluid elsewhere).
 The design column is the set of elements whose centroid has x, y in
 [0.25, 0.75] L and z in [0, 0.75 Lz].
 """
@@ -30,7 +32,23 @@ WORKLOADS = {
                                 patch="flux", design="smoothed_random", seed=3),
     "tall192x192x384_gr1e6": dict(nx=192, ny=192, nz=384, h=1 / 192, Gr=1e6, Pr=0.71,
                                   patch="flux", design="smoothed_random", seed=5),
+    # The paper's own set-up (Sec. 6.1-6.2): the quarter of a closed unit cavity
+    # (x, y in [0, 1/2], z in [0, 1] vertical; symmetry planes at x = y = 1/2),
+    # mesh 80 x 80 x 160 (the paper's 80 x 160 x 80 with its middle index
+    # vertical), Pr = 1, Ck = 1e-2, first continuation step q_f = 0.881,
+    # q_alpha = 8, alpha_max = 1e5, heat source block s0 = 1e4.
+    "quarter80x80x160_gr1e3": dict(nx=80, ny=80, nz=160, h=1 / 160, Gr=1e3, Pr=1.0,
+                                   patch="none", bcs="quarter", design="quarter", seed=7,
+                                   material=dict(alpha_max=1e5, q_alpha=8.0, q_f=0.881, Ck=1e-2)),
+    "quarter80x80x160_gr1e6": dict(nx=80, ny=80, nz=160, h=1 / 160, Gr=1e6, Pr=1.0,
+                                   patch="none", bcs="quarter", design="quarter", seed=7,
+                                   material=dict(alpha_max=1e5, q_alpha=8.0, q_f=0.881, Ck=1e-2)),
 }
+# Quarter-cavity geometry (fractions of the full unit cavity): heat-source block
+# 0.1 x 0.1 wide, 0.05 high at the centre of the bottom; design domain 0.75 x 0.75
+# wide and 0.75 high, sitting on top of the source block.
+QUARTER = dict(source_half=0.05, source_height=0.05, design_half=0.375, design_height=0.75,
+               s0=1e4, vf=0.05)
 # material parameters common to all workloads: RAMP q = 1, alpha_max = 1e4,
 # solid-to-fluid conductivity ratio 10 (Ck = k_f / k_s = 0.1)
 MATERIAL = dict(alpha_max=1e4, q_alpha=1.0, q_f=1.0, Ck=0.1)
@@ -91,10 +109,51 @@ def fins(nx, ny, nz, h, seed):
     return gam
 
 
+def quarter_regions(nx, ny, nz, h):
+    """Source-block and design-domain element masks of the quarter cavity, whose
+    symmetry planes are the faces x = nx h and y = ny h."""
+    c = elem_centroids(nx, ny, nz, h)
+    Lx, Ly = nx * h, ny * h
+    q = QUARTER
+    near = lambda half: (c[:, 0] >= Lx - half) & (c[:, 1] >= Ly - half)
+    src = near(q["source_half"]) & (c[:, 2] <= q["source_height"])
+    des = (near(q["design_half"]) & (c[:, 2] > q["source_height"])
+           & (c[:, 2] <= q["source_height"] + q["design_height"]))
+    return src, des
+
+
+def quarter_design(nx, ny, nz, h, seed):
+    """Solid source block (gamma = 0), the design domain at the volume fraction
+    of the paper (gamma = 1 - v_f, the uniform start of an optimisation) with
+    seeded smoothed noise of amplitude 0.02, fluid elsewhere."""
+    src, des = quarter_regions(nx, ny, nz, h)
+    rng = np.random.default_rng(seed)
+    noise = box_filter3(rng.uniform(-1.0, 1.0, size=(nz, ny, nx))).ravel()
+    g = np.ones(nx * ny * nz)
+    g[des] = np.clip(1.0 - QUARTER["vf"] + 0.02 * noise[des], 0.0, 1.0)
+    g[src] = 0.0
+    return g
+
+
+def source(name_or_cfg):
+    """Element heat source s_e: s0 in the source block of the quarter cavity."""
+    cfg = WORKLOADS[name_or_cfg] if isinstance(name_or_cfg, str) else name_or_cfg
+    s = np.zeros(cfg["nx"] * cfg["ny"] * cfg["nz"])
+    if cfg.get("bcs") == "quarter":
+        src, _ = quarter_regions(cfg["nx"], cfg["ny"], cfg["nz"], cfg["h"])
+        s[src] = QUARTER["s0"]
+    return s
+
+
+def material(name_or_cfg):
+    cfg = WORKLOADS[name_or_cfg] if isinstance(name_or_cfg, str) else name_or_cfg
+    return dict(cfg.get("material", MATERIAL))
+
+
 def design(name_or_cfg, seed=None):
     cfg = WORKLOADS[name_or_cfg] if isinstance(name_or_cfg, str) else name_or_cfg
     s = cfg["seed"] if seed is None else seed
-    gen = {"smoothed_random": smoothed_random, "fins": fins}[cfg["design"]]
+    gen = {"smoothed_random": smoothed_random, "fins": fins, "quarter": quarter_design}[cfg["design"]]
     return gen(cfg["nx"], cfg["ny"], cfg["nz"], cfg["h"], s)
 
 
@@ -106,7 +165,8 @@ def design_step(name_or_cfg, gam, seed, amp=0.02):
     nx, ny, nz, h = cfg["nx"], cfg["ny"], cfg["nz"], cfg["h"]
     rng = np.random.default_rng(seed)
     d = box_filter3(rng.uniform(-1.0, 1.0, size=(nz, ny, nx))).ravel()
-    col = design_column(nx, ny, nz, h)
+    col = (quarter_regions(nx, ny, nz, h)[1] if cfg.get("bcs") == "quarter"
+           else design_column(nx, ny, nz, h))
     out = np.array(gam, dtype=float, copy=True)
     out[col] = np.clip(out[col] + amp * d[col], 0.0, 1.0)
     return out

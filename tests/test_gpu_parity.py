@@ -142,6 +142,54 @@ def test_sensitivity_and_objective(nc, c):
         assert rel(host(g, g_o.shape), g_o) <= 1e-15
 
 
+def quarter_pair(nc, n=8, Gr=1e3):
+    """The paper's quarter cavity (symmetry planes, closed walls, pinned
+    pressure, heat-source block) at nx = ny = n, nz = 2n."""
+    nx, ny, nz, h = n, n, 2 * n, 1.0 / (2 * n)
+    cfg = dict(synth.WORKLOADS["quarter80x80x160_gr1e3"], nx=nx, ny=ny, nz=nz, h=h, Gr=Gr)
+    pin = (nx + 1) * (ny + 1) * nz
+    bc = G.BCs(vel_bc=(G.NOSLIP, G.SYMMETRY, G.NOSLIP, G.SYMMETRY, G.NOSLIP, G.NOSLIP),
+               T_bc=(G.DIRICHLET, G.ADIABATIC, G.DIRICHLET, G.ADIABATIC, G.ADIABATIC, G.DIRICHLET),
+               patch_mode=G.PATCH_NONE, p_pin=pin)
+    se = synth.source(cfg)
+    prob, _ = oracle_problem(nx, ny, nz, h, Gr, cfg["Pr"], bc=bc, se=se, **synth.material(cfg))
+    gp = nc.Problem(nc.make_params(nx, ny, nz, h, Gr, cfg["Pr"], **synth.material(cfg)),
+                    nc.quarter_bcs(nx, ny, nz))
+    gp.set_source(dev(se))
+    gam = synth.quarter_design(nx, ny, nz, h, 3)
+    return prob, bc, gp, gam
+
+
+def test_quarter_cavity_operators(nc):
+    prob, bc, gp, gam = quarter_pair(nc)
+    assert prob.se.sum() > 0 and (gam == 0).sum() >= 1
+    fl = gp.bc_flags()
+    for f in range(5):
+        assert np.array_equal(((fl >> f) & 1).astype(bool), prob.dmask[f])
+    x = random_bc_state(prob, 31)
+    xd, gd = dev(x), dev(gam)
+    assert rel(host(gp.residual(xd, gd), (5, -1)), prob.residual(x, gam)) <= TOL64
+    J = prob.jacobian(x, gam)
+    v = np.random.default_rng(32).standard_normal(prob.g.ndof)
+    assert rel(host(gp.jvp(xd, gd, dev(v))), J @ v) <= TOL64
+    assert rel(host(gp.jtvp(xd, gd, dev(v))), J.T @ v) <= TOL64
+    phi, g = gp.objective(xd)
+    phi_o, g_o = S.objective(prob, bc, x)
+    assert phi == pytest.approx(phi_o, rel=1e-13)
+    assert rel(host(g, g_o.shape), g_o) <= 1e-14
+    lam = np.random.default_rng(33).standard_normal((5, prob.g.Nn))
+    assert rel(host(gp.sensitivity(xd, gd, dev(lam))), S.sensitivity(prob, x, gam, lam)) <= TOL64
+
+
+def test_quarter_cavity_newton_matches_oracle(nc):
+    prob, bc, gp, gam = quarter_pair(nc)
+    xo, _ = S.newton(prob, gam, np.zeros((5, prob.g.Nn)), rtol=1e-12)
+    for mixed in (0, 1):
+        x = torch.zeros(gp.ndof, dtype=torch.float64, device="cuda")
+        _, info = gp.newton_solve(dev(gam), x, nc.default_opts(mixed=mixed, rtol_newton=1e-10))
+        assert rel(host(x), xo.ravel()) <= 1e-8, info
+
+
 def test_adjoint_dot_product_32cube(nc):
     """w^T (J v) = (J^T w)^T v at a size beyond the oracle's (32^3, FP64)."""
     n = 32

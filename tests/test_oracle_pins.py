@@ -269,6 +269,20 @@ def test_slab_flux_and_objective():
     assert dphi.sum() == pytest.approx(1.0, rel=1e-14)
 
 
+def test_thermal_compliance_closed_form():
+    """Sec. 3.2: f = int_omega s T dV.  For a uniform temperature T = c it is
+    c * sum_e s_e h^3, and its gradient sums to int s dV."""
+    bc = G.BCs(patch_mode=G.PATCH_NONE)
+    g = G.Grid(4, 3, 5, 0.2)
+    se = np.random.default_rng(12).uniform(0.0, 10.0, size=g.E)
+    _, bc, prob = make(4, 3, 5, 0.2, bc=bc, se=se)
+    x = np.zeros((5, g.Nn))
+    x[4] = 1.7
+    f, df = S.objective(prob, bc, x)
+    assert f == pytest.approx(1.7 * se.sum() * 0.2 ** 3, rel=1e-14)
+    assert df.sum() == pytest.approx(se.sum() * 0.2 ** 3, rel=1e-14)
+
+
 def test_line_search_closed_form():
     """Sec. 5.1: the step minimises the quadratic through the three norms."""
     for lam_true, c2 in ((0.3, 2.0), (0.8, 0.5), (0.02, 4.0)):
