@@ -253,8 +253,12 @@ def run_ours(args, rank, world):
     t_apply = t_step / NAPPLY * 1e-3
     achieved = flops / t_apply / 1e12
     peak = ALU_PEAK_TFLOPS[args.prec]
+    # DRAM bytes (read + write) of one element-kernel launch from the 128^3 ncu captures
+    # of this kernel version (profiles/k_elem_lin_cavity128.md), scaled by elements
+    traffic = {"f64": 196.46e6 + 2638.0e6, "f32": 96.55e6 + 278.28e6}[args.prec] \
+        * prob.E / 2097152
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
-            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": round(traffic),
             "kernel": "k_elem_lin<%s> + k_gather" % ("double" if dt == torch.float64 else "float"),
             "peak_source": "ALU unit counts x 2.07 GHz (FP32) / nominal FP64 rate"}
 

@@ -178,6 +178,18 @@ nc_status nc_sensitivity(nc_ctx* ctx, const double* x, const double* gamma,
 nc_status nc_jvp_static(const nc_params* prm, const nc_bcs* bcs, const void* x,
                         const void* gamma, const void* v, void* Jv, int prec, void* stream);
 
+/* PDE (Helmholtz) density filter (Sec. 3.2; [Lazarov & Sigmund 2011]; the paper
+ * uses radius = 2.5 h, Sec. 6.3-6.4): solves -r^2 lap(rho~) + rho~ = rho with
+ * zero normal derivative on the boundary, r = radius / (2 sqrt 3), trilinear
+ * nodal rho~ and element-constant rho, and returns the element means
+ * gamma_f[e] of rho~ (element arrays [E], FP64, device).  The map rho -> gamma_f
+ * is symmetric, so the same call applied to dPhi/dgamma_f gives dPhi/drho (the
+ * chain rule of the filtered design).  Conjugate gradients with Jacobi
+ * preconditioning to a relative residual of 1e-13; workspace (6 node vectors)
+ * is allocated at the first call.  Synchronous.  NC_ERR_NAN for a non-finite
+ * design, NC_ERR_MAXIT if CG does not converge in 1000 iterations. */
+nc_status nc_filter(nc_ctx* ctx, const double* rho, double* gamma_f, double radius, void* stream);
+
 /* Solver options.  rtol_newton: stop when ||R|| <= max(rtol_newton ||R_0||,
  * atol_newton) (Sec. 5.1 uses a relative tolerance);
  * rtol_lin: FGMRES relative tolerance per linear solve (Sec. 5.2); max_newton,

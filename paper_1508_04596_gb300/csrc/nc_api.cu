@@ -164,6 +164,7 @@ void nc_destroy(nc_ctx* ctx) {
   for (auto& p : ctx->tmp64) cudaFree(p);
   for (auto& p : ctx->tmp32) cudaFree(p);
   cudaFree(ctx->cjel);
+  for (auto& p : ctx->filt) cudaFree(p);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
   delete ctx;
 }

@@ -88,6 +88,7 @@ struct nc_ctx {
   double* cjel = nullptr;     // coarsest-level element Jacobians (40 x 40 per element)
   long long cjel_elems = 0;
   cudaStream_t cap = nullptr; // stream used to capture the V-cycle graph
+  double* filt[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // filter CG
   std::string err;
 };
 

@@ -1,0 +1,62 @@
+"""One design iteration of an optimisation run, for timing and profiling.
+
+    python -m paper_1508_04596_gb300.design_iteration WORKLOAD [--fp64] [--no-adjoint]
+
+Solves the state of the workload's design from a cold start, takes one
+synthetic optimiser step of the design (``synth.design_step``), then runs the
+warm-started Newton state solve, the objective, the adjoint solve and the
+element sensitivities (Sec. 3.2, Sec. 5) inside an NVTX range named "warm", so
+that a profiler can be restricted to it (``ncu --nvtx --nvtx-include warm/``).
+Prints the iteration counts and wall times of the warm part.
+"""
+import argparse
+import json
+import time
+
+import torch
+
+from . import nc, synth
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("workload")
+    ap.add_argument("--fp64", action="store_true", help="plain FP64 instead of mixed precision")
+    ap.add_argument("--no-adjoint", action="store_true")
+    a = ap.parse_args(argv)
+    mixed = 0 if a.fp64 else 1
+    prob = nc.Problem.from_workload(a.workload, patch="flux")
+    g0 = torch.tensor(synth.design(a.workload), dtype=torch.float64, device="cuda")
+    g1 = torch.tensor(synth.design_step(a.workload, synth.design(a.workload), 77),
+                      dtype=torch.float64, device="cuda")
+    x = torch.zeros(prob.ndof, dtype=torch.float64, device="cuda")
+    prob.newton_solve(g0, x, nc.default_opts(mixed=1, ramp_steps=3))
+    # load the kernels and allocate the workspace of this precision (untimed)
+    wopts = nc.default_opts(mixed=mixed, max_newton=1, max_lin=2)
+    xw = x.clone()
+    prob.newton_solve(g1, xw, wopts, check=False)
+    _, dw = prob.objective(xw)
+    lw, _ = prob.adjoint_solve(xw, g1, -dw, opts=wopts, check=False)
+    prob.sensitivity(xw, g1, lw)
+    del xw, dw, lw
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("warm")
+    t0 = time.perf_counter()
+    _, inf = prob.newton_solve(g1, x, nc.default_opts(mixed=mixed))
+    torch.cuda.synchronize()
+    out = {"workload": a.workload, "mixed": mixed, "state_s": time.perf_counter() - t0,
+           "newton_its": inf["newton_its"], "lin_its": inf["lin_its_total"]}
+    if not a.no_adjoint:
+        t0 = time.perf_counter()
+        phi, dphi = prob.objective(x)
+        lam, ainf = prob.adjoint_solve(x, g1, -dphi, opts=nc.default_opts(mixed=mixed))
+        prob.sensitivity(x, g1, lam)
+        torch.cuda.synchronize()
+        out.update(adjoint_plus_sens_s=time.perf_counter() - t0, phi=phi,
+                   adjoint_lin_its=ainf["lin_its_total"])
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -86,6 +86,7 @@ _SIGS = {
     "nc_objective": (ctypes.c_int, [_ctx, _vp, ctypes.POINTER(ctypes.c_double), _vp, _vp]),
     "nc_sensitivity": (ctypes.c_int, [_ctx, _vp, _vp, _vp, _vp, _vp]),
     "nc_default_opts": (None, [ctypes.POINTER(SolveOpts)]),
+    "nc_filter": (ctypes.c_int, [_ctx, _vp, _vp, ctypes.c_double, _vp]),
     "nc_newton_solve": (ctypes.c_int, [_ctx, _vp, _vp, ctypes.POINTER(SolveOpts),
                                        ctypes.POINTER(SolveInfo), _vp]),
     "nc_adjoint_solve": (ctypes.c_int, [_ctx, _vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts),
@@ -276,6 +277,16 @@ class Problem:
                                      _stream(stream)))
         return out
 
+    def filter(self, rho, radius=None, out=None, stream=None):
+        """PDE density filter (Sec. 3.2); radius defaults to 2.5 h (Sec. 6.3).
+        Symmetric: applied to dPhi/dgamma~ it returns dPhi/drho."""
+        out = torch.empty_like(rho) if out is None else out
+        R = 2.5 * self.params.h if radius is None else radius
+        self._chk(lib.nc_filter(self.ctx, self._vec(rho, torch.float64, self.E, "rho"),
+                                self._vec(out, torch.float64, self.E, "gamma_f"), R,
+                                _stream(stream)))
+        return out
+
     # ---- solvers ---------------------------------------------------------
     def newton_solve(self, gam, x, opts=None, stream=None, check=True):
         opts = default_opts() if opts is None else opts
@@ -299,6 +310,20 @@ class Problem:
         if check:
             self._chk(st)
         return lam, info.as_dict()
+
+
+class DensityFilter(torch.autograd.Function):
+    """gamma~ = P rho, the PDE density filter (Sec. 3.2); P is symmetric, so the
+    backward pass applies the same filter to the incoming gradient."""
+
+    @staticmethod
+    def forward(ctx, rho, prob, radius=None):
+        ctx.prob, ctx.radius = prob, radius
+        return prob.filter(rho.detach().contiguous(), radius)
+
+    @staticmethod
+    def backward(ctx, grad):
+        return ctx.prob.filter(grad.contiguous(), ctx.radius), None, None
 
 
 class PatchTemperature(torch.autograd.Function):

@@ -283,6 +283,56 @@ def test_thermal_compliance_closed_form():
     assert df.sum() == pytest.approx(se.sum() * 0.2 ** 3, rel=1e-14)
 
 
+def test_filter_element_matrices_closed_form():
+    """Sec. 3.2 filter: the Gauss-integrated Q1 element matrices equal the
+    textbook closed forms (stiffness h/3, 0, -h/12, -h/12; mass h^3/216 *
+    2^(number of shared coordinates))."""
+    from oracle import filter as F
+    h = 0.3
+    Ke, Me = F.element_matrices(h)
+    Kc = q1_laplace_stiffness(h)
+    for a in range(8):
+        for b in range(8):
+            nd = bin(a ^ b).count("1")
+            assert Me[a, b] == pytest.approx(h ** 3 / 216.0 * 2 ** (3 - nd), rel=1e-13)
+    assert np.allclose(Ke, Kc, rtol=1e-13, atol=1e-15)
+
+
+def test_filter_preserves_constants_and_volume():
+    """Neumann Helmholtz filter: a constant design is unchanged, and the
+    design volume sum_e gamma~_e h^3 equals sum_e rho_e h^3 for any rho."""
+    from oracle import filter as F
+    g = G.Grid(6, 5, 7, 0.1)
+    R = 2.5 * g.h
+    assert np.allclose(F.apply_filter(g, np.full(g.E, 0.37), R), 0.37, rtol=1e-12)
+    rho = np.random.default_rng(13).uniform(size=g.E)
+    gt = F.apply_filter(g, rho, R)
+    assert gt.sum() == pytest.approx(rho.sum(), rel=1e-12)
+    assert gt.std() < rho.std()  # it smooths
+
+
+def test_filter_cosine_mode_decay():
+    """A cosine mode cos(k pi x / L) satisfies the Neumann condition and is an
+    eigenfunction of -r^2 lap + 1: it is damped by 1/(1 + r^2 (k pi / L)^2),
+    recovered to second order in h."""
+    from oracle import filter as F
+    errs = []
+    for n in (16, 32):
+        g = G.Grid(n, 2, 2, 1.0 / n)
+        R = 0.1
+        r2 = (R / (2 * np.sqrt(3))) ** 2
+        c = g.elem_centroids()
+        k = 2
+        # element averages of the mode (exact cell averages of cos in x)
+        x0, x1 = c[:, 0] - g.h / 2, c[:, 0] + g.h / 2
+        rho = (np.sin(k * np.pi * x1) - np.sin(k * np.pi * x0)) / (k * np.pi * g.h)
+        gt = F.apply_filter(g, rho, R)
+        expect = rho / (1.0 + r2 * (k * np.pi) ** 2)
+        errs.append(np.abs(gt - expect).max())
+    assert errs[1] < errs[0] / 3.0, errs
+    assert errs[1] < 1e-2
+
+
 def test_line_search_closed_form():
     """Sec. 5.1: the step minimises the quadratic through the three norms."""
     for lam_true, c2 in ((0.3, 2.0), (0.8, 0.5), (0.02, 4.0)):
