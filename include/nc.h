@@ -220,7 +220,7 @@ typedef struct {
 } nc_solve_info;
 
 /* Fill opts with defaults (rtol_newton 1e-8, rtol_lin 1e-5, max_newton 30,
- * max_lin 200, restart 30, all levels, smooth_its 4, coarse_its 30, mixed 1,
+ * max_lin 200, restart 30, all levels, smooth_its 6, coarse_its 30, mixed 1,
  * ramp_steps 0). */
 void nc_default_opts(nc_solve_opts* opts);
 

@@ -577,7 +577,7 @@ void nc_default_opts(nc_solve_opts* o) {
   o->max_lin = 200;
   o->restart = 30;
   o->mg_levels = 0;
-  o->smooth_its = 4;
+  o->smooth_its = 6;
   o->coarse_its = 30;
   o->mixed = 1;
   o->ramp_steps = 0;
