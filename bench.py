@@ -32,7 +32,8 @@ NAPPLY = 16  # J v applications per step
 # Operation counts per element (one +, -, * or / = 1 flop; an FMA = 2), of the
 # element routines in csrc/nc_element.cuh, counted by instantiating them with a
 # counting number type.
-FLOPS_PER_ELEM = {"residual": 3038, "jvp": 4950, "jtvp": 4718, "diag": 7293, "sens": 4281}
+FLOPS_PER_ELEM = {"residual": 3038, "jvp": 4950, "jtvp": 4718, "diag": 7293, "sens": 4282,
+                  "linearize": 1266, "jvp_lin": 3698}
 # ALU peaks (whole GPU): FP32 = 152 SM x 128 lanes x 2 flop x 2.07 GHz; FP64 = the
 # GB300's nominal 1.25 TFLOP/s (equal to our FMA-chain probe on the box: 78.5 and
 # 1.25 TFLOP/s measured).
@@ -218,9 +219,17 @@ def run_ours(args, rank, world):
     out = torch.empty_like(xj)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
 
-    def step():
-        for i in range(NAPPLY):
-            prob.jvp(xj, gj, V[i], out)
+    if args.prec == "f64":
+        # a step: linearise at the state once, then NAPPLY products (the use in a
+        # Krylov solve); the linearisation is inside the timed region
+        def step():
+            prob.linearize(xj, gj)
+            for i in range(NAPPLY):
+                prob.jvp_lin(V[i], out)
+    else:
+        def step():
+            for i in range(NAPPLY):
+                prob.jvp(xj, gj, V[i], out)
 
     for _ in range(args.warmup):
         step()
@@ -248,18 +257,23 @@ def run_ours(args, rank, world):
         dist.barrier()
     value = world * NAPPLY * ndof / (t_step * 1e-3) / 1e9
 
-    # --- roofline of the dominant kernel (the J v element kernel + owner gather)
-    flops = FLOPS_PER_ELEM["jvp"] * prob.E
-    t_apply = t_step / NAPPLY * 1e-3
-    achieved = flops / t_apply / 1e12
+    # --- roofline of the dominant kernel (the J v element kernel + owner gather; in FP64
+    # the linearisation that the step computes once is counted with it)
+    if args.prec == "f64":
+        flops = (FLOPS_PER_ELEM["jvp_lin"] * NAPPLY + FLOPS_PER_ELEM["linearize"]) * prob.E
+    else:
+        flops = FLOPS_PER_ELEM["jvp"] * NAPPLY * prob.E
+    achieved = flops / (t_step * 1e-3) / 1e12
     peak = ALU_PEAK_TFLOPS[args.prec]
     # DRAM bytes (read + write) of one element-kernel launch from the 128^3 ncu captures
     # of this kernel version (profiles/k_elem_lin_cavity128.md), scaled by elements
-    traffic = {"f64": 196.46e6 + 2638.0e6, "f32": 96.55e6 + 278.28e6}[args.prec] \
+    traffic = {"f64": 2750.17e6 + 1033.92e6, "f32": 96.55e6 + 278.28e6}[args.prec] \
         * prob.E / 2097152
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
-            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": round(traffic),
-            "kernel": "k_elem_lin<%s> + k_gather" % ("double" if dt == torch.float64 else "float"),
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+            "traffic": None if traffic is None else round(traffic),
+            "kernel": ("k_elem_lin_cached<double> + k_gather, k_elem_linearize once per step"
+                       if args.prec == "f64" else "k_elem_lin<float> + k_gather"),
             "peak_source": "ALU unit counts x 2.07 GHz (FP32) / nominal FP64 rate"}
 
     # --- end to end through the C ABI with host buffers
@@ -273,8 +287,13 @@ def run_ours(args, rank, world):
         xd.copy_(xh, non_blocking=True)
         gd.copy_(gh, non_blocking=True)
         Vd.copy_(Vh, non_blocking=True)
-        for i in range(NAPPLY):
-            prob.jvp(xd, gd, Vd[i], od[i])
+        if args.prec == "f64":
+            prob.linearize(xd, gd)
+            for i in range(NAPPLY):
+                prob.jvp_lin(Vd[i], od[i])
+        else:
+            for i in range(NAPPLY):
+                prob.jvp(xd, gd, Vd[i], od[i])
         outh.copy_(od, non_blocking=True)
 
     for _ in range(2):
@@ -297,10 +316,12 @@ def run_ours(args, rank, world):
     # --- other operators at the same state (for context)
     ops = {}
     x32, g32, v32 = x.float(), gam64.float(), V[0].float()
-    o32 = torch.empty_like(x32)
-    for name, fn in (("residual", lambda: prob.residual(xj, gj, out)),
-                     ("jtvp", lambda: prob.jtvp(xj, gj, V[0], out)),
-                     ("diag", lambda: prob.diag(xj, gj, out)),
+    x64, v64 = x.double(), V[0].double()
+    o32, o64 = torch.empty_like(x32), torch.empty_like(x64)
+    for name, fn in (("residual", lambda: prob.residual(x64, gam64, o64)),
+                     ("jvp", lambda: prob.jvp(x64, gam64, v64, o64)),
+                     ("jtvp", lambda: prob.jtvp(x64, gam64, v64, o64)),
+                     ("diag", lambda: prob.diag(x64, gam64, o64)),
                      ("jvp_f32", lambda: prob.jvp(x32, g32, v32, o32)),
                      ("residual_f32", lambda: prob.residual(x32, g32, o32))):
         for _ in range(3):
@@ -313,7 +334,7 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         t = a.elapsed_time(b) / 5
         base = name.replace("_f32", "")
-        pk = ALU_PEAK_TFLOPS["f32"] if name.endswith("_f32") else peak
+        pk = ALU_PEAK_TFLOPS["f32"] if name.endswith("_f32") else ALU_PEAK_TFLOPS["f64"]
         ops[name] = {"ms": round(t, 4), "gdofs": round(ndof / t / 1e6, 3),
                      "alu_frac": round(FLOPS_PER_ELEM[base] * prob.E / (t * 1e-3) / 1e12 / pk, 4)}
     extra["operators"] = ops
@@ -331,7 +352,7 @@ def run_ours(args, rank, world):
                        "Gr": cfg["Gr"], "Pr": cfg["Pr"], "jv_per_step": NAPPLY,
                        "l2": "flushed between steps (256 MB write)",
                        "parallelism": "replicas" if world > 1 else "single-gpu"},
-            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": 2 * NAPPLY * args.steps,
+            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": (2 * NAPPLY + (1 if args.prec == "f64" else 0)) * args.steps,
             "roofline": roof, "cpu_baseline": cpu}
     line.update(extra)
     return line

@@ -135,6 +135,19 @@ nc_status nc_jvp(nc_ctx* ctx, const void* x, const void* gamma, const void* v, v
 nc_status nc_jtvp(nc_ctx* ctx, const void* x, const void* gamma, const void* w, void* JTw,
                   int prec, void* stream);
 
+/* Linearised products (FP64).  nc_linearize stores, for the state x and design
+ * gamma, the state-only part of every quadrature point (velocity, velocity
+ * gradient, temperature gradient and the strong residuals) and each element's
+ * stabilisation parameters; nc_jvp_lin / nc_jtvp_lin then give the same J v and
+ * J^T w as nc_jvp / nc_jtvp at that state without re-interpolating it -- the
+ * products a Krylov solve applies many times at one state.  x and gamma are not
+ * copied: they must stay unchanged while the linearisation is used.  The store
+ * (about 1.2 KB per element) is allocated at the first call.  NC_ERR_ARG if
+ * nc_jvp_lin / nc_jtvp_lin come before any nc_linearize. */
+nc_status nc_linearize(nc_ctx* ctx, const double* x, const double* gamma, void* stream);
+nc_status nc_jvp_lin(nc_ctx* ctx, const double* v, double* Jv, void* stream);
+nc_status nc_jtvp_lin(nc_ctx* ctx, const double* w, double* JTw, void* stream);
+
 /* d = diag(J(x, gamma)) (1 on Dirichlet rows): the Jacobi scaling of the
  * multigrid smoother (Sec. 5.2). */
 nc_status nc_diag(nc_ctx* ctx, const void* x, const void* gamma, void* d, int prec,

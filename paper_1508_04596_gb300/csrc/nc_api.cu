@@ -115,6 +115,10 @@ void free_level(Level& L) {
   cudaFree(L.f32.inv);
   L.f64.inv = nullptr;
   L.f32.inv = nullptr;
+  cudaFree(L.f64.lin);
+  cudaFree(L.f32.lin);
+  L.f64.lin = nullptr;
+  L.f32.lin = nullptr;
 }
 
 bool check_prec(int prec) { return prec == NC_FP64 || prec == NC_FP32; }
@@ -165,6 +169,7 @@ void nc_destroy(nc_ctx* ctx) {
   for (auto& p : ctx->tmp32) cudaFree(p);
   cudaFree(ctx->cjel);
   for (auto& p : ctx->filt) cudaFree(p);
+  cudaFree(ctx->pub_lin);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
   delete ctx;
 }
@@ -333,6 +338,37 @@ nc_status nc_diag(nc_ctx* ctx, const void* x, const void* gam, void* d, int prec
   else
     op_diag(L.d, L.c32, (const float*)x, (const float*)gam, L.f32.src, (float*)d, (float*)ctx->Y, s);
   return cuda_check(ctx, cudaGetLastError(), "nc_diag");
+}
+
+nc_status nc_linearize(nc_ctx* ctx, const double* x, const double* gam, void* stream) {
+  if (!ctx || !x || !gam) return set_err(ctx, NC_ERR_ARG, "nc_linearize: bad argument");
+  const Level& L = ctx->lv[0];
+  nc_status st;
+  if (!ctx->pub_lin &&
+      (st = dev_alloc(ctx, &ctx->pub_lin, (long long)LIN_SLOTS * L.d.E)) != NC_OK)
+    return st;
+  op_linearize<double>(L.d, L.c64, x, gam, L.f64.src, ctx->pub_lin, (cudaStream_t)stream);
+  ctx->pub_x = x;
+  ctx->pub_gam = gam;
+  return cuda_check(ctx, cudaGetLastError(), "nc_linearize");
+}
+
+nc_status nc_jvp_lin(nc_ctx* ctx, const double* v, double* Jv, void* stream) {
+  if (!ctx || !v || !Jv) return set_err(ctx, NC_ERR_ARG, "nc_jvp_lin: bad argument");
+  if (!ctx->pub_x) return set_err(ctx, NC_ERR_ARG, "nc_jvp_lin: call nc_linearize first");
+  const Level& L = ctx->lv[0];
+  op_jvp_cached<double>(L.d, L.c64, ctx->pub_x, ctx->pub_gam, L.f64.src, ctx->pub_lin, v, Jv,
+                        ctx->Y, (cudaStream_t)stream);
+  return cuda_check(ctx, cudaGetLastError(), "nc_jvp_lin");
+}
+
+nc_status nc_jtvp_lin(nc_ctx* ctx, const double* w, double* JTw, void* stream) {
+  if (!ctx || !w || !JTw) return set_err(ctx, NC_ERR_ARG, "nc_jtvp_lin: bad argument");
+  if (!ctx->pub_x) return set_err(ctx, NC_ERR_ARG, "nc_jtvp_lin: call nc_linearize first");
+  const Level& L = ctx->lv[0];
+  op_jtvp_cached<double>(L.d, L.c64, ctx->pub_x, ctx->pub_gam, L.f64.src, ctx->pub_lin, w, JTw,
+                         ctx->Y, (cudaStream_t)stream);
+  return cuda_check(ctx, cudaGetLastError(), "nc_jtvp_lin");
 }
 
 nc_status nc_objective(nc_ctx* ctx, const double* x, double* phi_host, double* dphidx,

@@ -332,10 +332,9 @@ NC_HD void elem_residual(const R xe[5][8], R gam, R s, const ElemConst<R>& c, R 
 // the parameter directions (dalpha, dK, dtau, dtauT); returns w-scaled f0 and
 // (w/h)-scaled F1.
 template <typename R>
-NC_HD void flux_tangent(const QP<R>& q, const QP<R>& d, const ElemCoef<R>& k, R dalpha, R dK,
-                        R dtau, R dtauT, const ElemConst<R>& c, R f0[5], R F1[5][3]) {
-  R conv[3], rM[3], rT;
-  strong(q, k, c, conv, rM, rT);
+NC_HD void flux_tangent_rm(const QP<R>& q, const R rM[3], R rT, const QP<R>& d,
+                           const ElemCoef<R>& k, R dalpha, R dK, R dtau, R dtauT,
+                           const ElemConst<R>& c, R f0[5], R F1[5][3]) {
   R dconv[3], drM[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -365,6 +364,14 @@ NC_HD void flux_tangent(const QP<R>& q, const QP<R>& d, const ElemCoef<R>& k, R 
 #pragma unroll
   for (int j = 0; j < 3; ++j)
     F1[4][j] = wh * (k.K * d.gT[j] + dK * q.gT[j] + q.u[j] * aT + d.u[j] * bT);
+}
+
+template <typename R>
+NC_HD void flux_tangent(const QP<R>& q, const QP<R>& d, const ElemCoef<R>& k, R dalpha, R dK,
+                        R dtau, R dtauT, const ElemConst<R>& c, R f0[5], R F1[5][3]) {
+  R conv[3], rM[3], rT;
+  strong(q, k, c, conv, rM, rT);
+  flux_tangent_rm(q, rM, rT, d, k, dalpha, dK, dtau, dtauT, c, f0, F1);
 }
 
 template <typename R>
@@ -403,10 +410,9 @@ NC_HD void elem_jvp(const R xe[5][8], const R ve[5][8], R gam, R s, const ElemCo
 // f0 (value slots) and F1 (gradient slots, times 1/h) for the test-side
 // transpose, plus the cotangents of tau and tau_T accumulated.
 template <typename R>
-NC_HD void flux_adjoint(const QP<R>& q, const QP<R>& t, const ElemCoef<R>& k,
-                        const ElemConst<R>& c, R f0[5], R F1[5][3], R& tau_bar, R& tauT_bar) {
-  R conv[3], rM[3], rT;
-  strong(q, k, c, conv, rM, rT);
+NC_HD void flux_adjoint_rm(const QP<R>& q, const R rM[3], R rT, const QP<R>& t,
+                           const ElemCoef<R>& k, const ElemConst<R>& c, R f0[5], R F1[5][3],
+                           R& tau_bar, R& tauT_bar) {
   const R w = c.wq;
   R c0[5] = {w * t.u[0], w * t.u[1], w * t.u[2], w * t.p, w * t.T};
   R C1[5][3];
@@ -471,6 +477,14 @@ NC_HD void flux_adjoint(const QP<R>& q, const QP<R>& t, const ElemCoef<R>& k,
   F1[4][0] = gTb[0] * ih;
   F1[4][1] = gTb[1] * ih;
   F1[4][2] = gTb[2] * ih;
+}
+
+template <typename R>
+NC_HD void flux_adjoint(const QP<R>& q, const QP<R>& t, const ElemCoef<R>& k,
+                        const ElemConst<R>& c, R f0[5], R F1[5][3], R& tau_bar, R& tauT_bar) {
+  R conv[3], rM[3], rT;
+  strong(q, k, c, conv, rM, rT);
+  flux_adjoint_rm(q, rM, rT, t, k, c, f0, F1, tau_bar, tauT_bar);
 }
 
 template <typename R>
@@ -550,6 +564,153 @@ NC_HD R elem_sens(const R xe[5][8], const R le[5][8], R gam, R s, const ElemCons
   R acc = R(0);
   NC_FOR_PAIRS(acc += pair_sens<R>(xe, le, k, da, dK, dtau, dtauT, c, cy, cz))
   return acc;
+}
+
+// ---------------------------------------------------------------------------- linearisation cache
+// In a Krylov solve J is applied many times at one state.  The state-only part
+// of every Gauss point -- u, grad u, grad T and the strong residuals rM, rT --
+// and the element's tau, tau_T can be computed once per linearisation and read
+// back by each product instead of being re-interpolated.  Layout: point g' =
+// 2 * pair + qx (pairs in the order (qy, qz) = (0,0), (1,0), (0,1), (1,1)),
+// LIN_GP values per point (u[3], G[3][3], gT[3], rM[3], rT), then tau, tau_T;
+// slot s of an element is stored at cache[s * stride].
+constexpr int LIN_GP = 19;
+constexpr int LIN_SLOTS = 8 * LIN_GP + 2;
+
+template <typename R, int P>
+NC_HD void pair_linearize(const R xe[5][8], const ElemCoef<R>& k, const ElemConst<R>& c,
+                          R* cache, long long stride) {
+  QP<R> q[2];
+  interp_all_pair<R>(xe, c.inv_h, R(gw(P & 1)), R(gw(P >> 1)), q);
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    R conv[3], rM[3], rT;
+    strong(q[s], k, c, conv, rM, rT);
+    R* o = cache + (long long)((2 * P + s) * LIN_GP) * stride;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o[i * stride] = q[s].u[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) o[(3 + 3 * i + j) * stride] = q[s].G[i][j];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) o[(12 + j) * stride] = q[s].gT[j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o[(15 + i) * stride] = rM[i];
+    o[18 * stride] = rT;
+  }
+}
+
+template <typename R>
+NC_HD void elem_linearize(const R xe[5][8], R gam, R s, const ElemConst<R>& c, R* cache,
+                          long long stride) {
+  R S;
+  ElemCoef<R> k = elem_coef(xe, gam, s, c, S);
+  pair_linearize<R, 0>(xe, k, c, cache, stride);
+  pair_linearize<R, 1>(xe, k, c, cache, stride);
+  pair_linearize<R, 2>(xe, k, c, cache, stride);
+  pair_linearize<R, 3>(xe, k, c, cache, stride);
+  cache[(long long)(8 * LIN_GP) * stride] = k.tau;
+  cache[(long long)(8 * LIN_GP + 1) * stride] = k.tauT;
+}
+
+template <typename R, int P>
+NC_HD void load_lin(const R* cache, long long stride, QP<R> q[2], R rM[2][3], R rT[2]) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const R* o = cache + (long long)((2 * P + s) * LIN_GP) * stride;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) q[s].u[i] = o[i * stride];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) q[s].G[i][j] = o[(3 + 3 * i + j) * stride];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) q[s].gT[j] = o[(12 + j) * stride];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) rM[s][i] = o[(15 + i) * stride];
+    rT[s] = o[18 * stride];
+    q[s].p = q[s].T = R(0);  // not needed once rM, rT are known
+#pragma unroll
+    for (int i = 0; i < 3; ++i) q[s].gp[i] = R(0);
+  }
+}
+
+template <typename R>
+NC_HD ElemCoef<R> lin_coef(const R* cache, long long stride, R gam, R s, const ElemConst<R>& c) {
+  ElemCoef<R> k;
+  k.alpha = alpha_of(gam, c);
+  k.K = K_of(gam, c);
+  k.tau = cache[(long long)(8 * LIN_GP) * stride];
+  k.tauT = cache[(long long)(8 * LIN_GP + 1) * stride];
+  k.s = s;
+  return k;
+}
+
+template <typename R, int P>
+NC_HD void pair_jvp_lin(const R* cache, long long stride, const R ve[5][8], const ElemCoef<R>& k,
+                        R dtau, R dtauT, const ElemConst<R>& c, R out[5][8]) {
+  QP<R> q[2], d[2];
+  R rM[2][3], rT[2];
+  load_lin<R, P>(cache, stride, q, rM, rT);
+  const R cy = R(gw(P & 1)), cz = R(gw(P >> 1));
+  interp_all_pair<R>(ve, c.inv_h, cy, cz, d);
+  R f0[2][5], F1[2][5][3];
+  flux_tangent_rm(q[0], rM[0], rT[0], d[0], k, R(0), R(0), dtau, dtauT, c, f0[0], F1[0]);
+  flux_tangent_rm(q[1], rM[1], rT[1], d[1], k, R(0), R(0), dtau, dtauT, c, f0[1], F1[1]);
+  test_all_pair<R>(out, cy, cz, f0, F1);
+}
+
+// J_e v_e from the linearisation cache; ue holds the element's nodal velocities
+// (needed for dtau/du_e . v_e).
+template <typename R>
+NC_HD void elem_jvp_lin(const R* cache, long long stride, const R ue[3][8], const R ve[5][8],
+                        R gam, R s, const ElemConst<R>& c, R out[5][8]) {
+  const ElemCoef<R> k = lin_coef(cache, stride, gam, s, c);
+  R uv = R(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int a = 0; a < 8; ++a) uv += ue[i][a] * ve[i][a];
+  const R dtau = -k.tau * k.tau * k.tau * c.inv16h2 * uv;
+  const R dtauT = -k.tauT * k.tauT * k.tauT * c.inv16h2 * uv;
+  zero_out(out);
+  pair_jvp_lin<R, 0>(cache, stride, ve, k, dtau, dtauT, c, out);
+  pair_jvp_lin<R, 1>(cache, stride, ve, k, dtau, dtauT, c, out);
+  pair_jvp_lin<R, 2>(cache, stride, ve, k, dtau, dtauT, c, out);
+  pair_jvp_lin<R, 3>(cache, stride, ve, k, dtau, dtauT, c, out);
+}
+
+template <typename R, int P>
+NC_HD void pair_jtvp_lin(const R* cache, long long stride, const R we[5][8],
+                         const ElemCoef<R>& k, const ElemConst<R>& c, R out[5][8], R& tau_bar,
+                         R& tauT_bar) {
+  QP<R> q[2], t[2];
+  R rM[2][3], rT[2];
+  load_lin<R, P>(cache, stride, q, rM, rT);
+  const R cy = R(gw(P & 1)), cz = R(gw(P >> 1));
+  interp_all_pair<R>(we, c.inv_h, cy, cz, t);
+  R f0[2][5], F1[2][5][3];
+  flux_adjoint_rm(q[0], rM[0], rT[0], t[0], k, c, f0[0], F1[0], tau_bar, tauT_bar);
+  flux_adjoint_rm(q[1], rM[1], rT[1], t[1], k, c, f0[1], F1[1], tau_bar, tauT_bar);
+  test_all_pair<R>(out, cy, cz, f0, F1);
+}
+
+template <typename R>
+NC_HD void elem_jtvp_lin(const R* cache, long long stride, const R ue[3][8], const R we[5][8],
+                         R gam, R s, const ElemConst<R>& c, R out[5][8]) {
+  const ElemCoef<R> k = lin_coef(cache, stride, gam, s, c);
+  zero_out(out);
+  R tb = R(0), tbT = R(0);
+  pair_jtvp_lin<R, 0>(cache, stride, we, k, c, out, tb, tbT);
+  pair_jtvp_lin<R, 1>(cache, stride, we, k, c, out, tb, tbT);
+  pair_jtvp_lin<R, 2>(cache, stride, we, k, c, out, tb, tbT);
+  pair_jtvp_lin<R, 3>(cache, stride, we, k, c, out, tb, tbT);
+  const R gsum = -(k.tau * k.tau * k.tau * tb + k.tauT * k.tauT * k.tauT * tbT) * c.inv16h2;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int a = 0; a < 8; ++a) out[i][a] += gsum * ue[i][a];
 }
 
 // ---------------------------------------------------------------------------- diagonal

@@ -51,6 +51,7 @@ struct LevelBuf {
   int ks = 0;
   bool ext = false;    // x and gam point to caller/Newton arrays (level 0, FP64)
   R* inv = nullptr;    // dense inverse of the level operator (coarsest level only)
+  R* lin = nullptr;    // linearisation cache (FP64 levels)
 };
 
 struct Level {
@@ -89,6 +90,9 @@ struct nc_ctx {
   long long cjel_elems = 0;
   cudaStream_t cap = nullptr; // stream used to capture the V-cycle graph
   double* filt[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // filter CG
+  double* pub_lin = nullptr;  // linearisation of nc_linearize (level 0, FP64)
+  const double* pub_x = nullptr;
+  const double* pub_gam = nullptr;
   std::string err;
 };
 
@@ -104,6 +108,17 @@ void op_jvp(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam, 
 template <typename R>
 void op_jtvp(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam, const R* src,
              const R* w, R* out, R* Y, cudaStream_t s);
+// linearisation cache (LIN_SLOTS values per element, slot-major) and the
+// products that read it
+template <typename R>
+void op_linearize(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam, const R* src,
+                  R* cache, cudaStream_t s);
+template <typename R>
+void op_jvp_cached(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam,
+                   const R* src, const R* cache, const R* v, R* out, R* Y, cudaStream_t s);
+template <typename R>
+void op_jtvp_cached(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam,
+                    const R* src, const R* cache, const R* w, R* out, R* Y, cudaStream_t s);
 template <typename R>
 void op_diag(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam, const R* src,
              R* out, R* Y, cudaStream_t s);

@@ -80,6 +80,51 @@ __global__ void __launch_bounds__(ELEM_THREADS) k_elem_lin(LevelDev d, ElemConst
 }
 
 template <typename R>
+__global__ void __launch_bounds__(ELEM_THREADS) k_elem_linearize(LevelDev d, ElemConst<R> c,
+                                                                 const R* __restrict__ x,
+                                                                 const R* __restrict__ gam,
+                                                                 const R* __restrict__ src,
+                                                                 R* cache) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= d.E) return;
+  R xe[5][8];
+  load_elem(d, x, e, xe, false);
+  elem_linearize<R>(xe, gam[e], src ? src[e] : R(0), c, cache + e, d.E);
+}
+
+// J v / J^T w from the linearisation cache: only the direction and the nodal
+// velocities of the state are gathered.
+template <typename R, bool TRANSPOSE>
+__global__ void __launch_bounds__(ELEM_THREADS) k_elem_lin_cached(
+    LevelDev d, ElemConst<R> c, const R* __restrict__ x, const R* __restrict__ gam,
+    const R* __restrict__ src, const R* __restrict__ cache, const R* __restrict__ v, R* Y) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= d.E) return;
+  R ue[3][8], ve[5][8], out[5][8];
+  {
+    const int i = (int)(e % d.nx);
+    const long long t = e / d.nx;
+    const int j = (int)(t % d.ny);
+    const int k = (int)(t / d.ny);
+    const long long n0 = node_id(d, i, j, k);
+    const long long sy = d.nx + 1, sz = (long long)(d.nx + 1) * (d.ny + 1);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const long long n = n0 + (a & 1) + ((a >> 1) & 1) * sy + ((a >> 2) & 1) * sz;
+#pragma unroll
+      for (int f = 0; f < 3; ++f) ue[f][a] = x[f * d.Nn + n];
+    }
+  }
+  load_elem(d, v, e, ve, true);  // Dirichlet columns removed
+  const R g = gam[e], s = src ? src[e] : R(0);
+  if (TRANSPOSE)
+    elem_jtvp_lin<R>(cache + e, d.E, ue, ve, g, s, c, out);
+  else
+    elem_jvp_lin<R>(cache + e, d.E, ue, ve, g, s, c, out);
+  store_elem(d.E, e, out, Y);
+}
+
+template <typename R>
 __global__ void __launch_bounds__(ELEM_THREADS) k_elem_diag(LevelDev d, ElemConst<R> c,
                                                             const R* __restrict__ x,
                                                             const R* __restrict__ gam,
@@ -327,6 +372,28 @@ void op_jtvp(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam,
 }
 
 template <typename R>
+void op_linearize(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam, const R* src,
+                  R* cache, cudaStream_t s) {
+  k_elem_linearize<R><<<nblocks(d.E, ELEM_THREADS), ELEM_THREADS, 0, s>>>(d, c, x, gam, src, cache);
+}
+
+template <typename R>
+void op_jvp_cached(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam,
+                   const R* src, const R* cache, const R* v, R* out, R* Y, cudaStream_t s) {
+  k_elem_lin_cached<R, false><<<nblocks(d.E, ELEM_THREADS), ELEM_THREADS, 0, s>>>(d, c, x, gam, src,
+                                                                                 cache, v, Y);
+  k_gather<R, G_LIN><<<nblocks(d.Nn, NODE_THREADS), NODE_THREADS, 0, s>>>(d, Y, v, out);
+}
+
+template <typename R>
+void op_jtvp_cached(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam,
+                    const R* src, const R* cache, const R* w, R* out, R* Y, cudaStream_t s) {
+  k_elem_lin_cached<R, true><<<nblocks(d.E, ELEM_THREADS), ELEM_THREADS, 0, s>>>(d, c, x, gam, src,
+                                                                                cache, w, Y);
+  k_gather<R, G_LIN><<<nblocks(d.Nn, NODE_THREADS), NODE_THREADS, 0, s>>>(d, Y, w, out);
+}
+
+template <typename R>
 void op_diag(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam, const R* src,
              R* out, R* Y, cudaStream_t s) {
   k_elem_diag<R><<<nblocks(d.E, ELEM_THREADS), ELEM_THREADS, 0, s>>>(d, c, x, gam, src, Y);
@@ -394,6 +461,12 @@ void op_coarsen_elem(const LevelDev& fine, const R* gf, const LevelDev& coarse, 
                            const R*, R*, R*, cudaStream_t);                                     \
   template void op_diag<R>(const LevelDev&, const ElemConst<R>&, const R*, const R*, const R*,  \
                            R*, R*, cudaStream_t);                                               \
+  template void op_linearize<R>(const LevelDev&, const ElemConst<R>&, const R*, const R*,       \
+                                const R*, R*, cudaStream_t);                                    \
+  template void op_jvp_cached<R>(const LevelDev&, const ElemConst<R>&, const R*, const R*,      \
+                                 const R*, const R*, const R*, R*, R*, cudaStream_t);           \
+  template void op_jtvp_cached<R>(const LevelDev&, const ElemConst<R>&, const R*, const R*,     \
+                                  const R*, const R*, const R*, R*, R*, cudaStream_t);          \
   template void op_impose<R>(const LevelDev&, R*, cudaStream_t);                                \
   template void op_mask<R>(const LevelDev&, R*, cudaStream_t);                                  \
   template void op_restrict<R>(const LevelDev&, const R*, const LevelDev&, R*, cudaStream_t);   \

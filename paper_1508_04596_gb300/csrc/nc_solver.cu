@@ -90,6 +90,13 @@ template <typename R>
 void level_apply(nc_ctx* ctx, int l, bool tr, const R* v, R* out, cudaStream_t s) {
   Level& L = ctx->lv[l];
   LevelBuf<R>& B = buf<R>(L);
+  if (B.lin) {  // FP64 levels: products from the linearisation cache
+    if (tr)
+      op_jtvp_cached<R>(L.d, cst<R>(L), B.x, B.gam, B.src, B.lin, v, out, (R*)ctx->Y, s);
+    else
+      op_jvp_cached<R>(L.d, cst<R>(L), B.x, B.gam, B.src, B.lin, v, out, (R*)ctx->Y, s);
+    return;
+  }
   if (tr)
     op_jtvp<R>(L.d, cst<R>(L), B.x, B.gam, B.src, v, out, (R*)ctx->Y, s);
   else
@@ -172,6 +179,9 @@ nc_status alloc_levels(nc_ctx* ctx, int nlev, const nc_solve_opts& o) {
         (st = alloc(ctx, &B.z, n)) != NC_OK || (st = alloc(ctx, &B.r, n)) != NC_OK ||
         (st = alloc(ctx, &B.t, n)) != NC_OK || (st = alloc(ctx, &B.Hd, (long long)HD_SIZE)) != NC_OK)
       return st;
+    if (sizeof(R) == sizeof(double) &&
+        (st = alloc(ctx, &B.lin, (long long)LIN_SLOTS * L.d.E)) != NC_OK)
+      return st;
     const bool level0_f64 = (l == 0) && sizeof(R) == sizeof(double);
     if (!level0_f64) {
       if ((st = alloc(ctx, &B.x, n)) != NC_OK || (st = alloc(ctx, &B.gam, L.d.E)) != NC_OK)
@@ -205,6 +215,7 @@ nc_status linearize(nc_ctx* ctx, int nlev, const double* x, const double* gam, c
     }
     // diag(J^T) = diag(J)
     op_diag<R>(L.d, cst<R>(L), B.x, B.gam, B.src, B.diag, (R*)ctx->Y, s);
+    if (B.lin) op_linearize<R>(L.d, cst<R>(L), B.x, B.gam, B.src, B.lin, s);
     if (l == nlev - 1 && coarse_dense_dofs(L) <= COARSE_DENSE_MAX) {
       const nc_status st = coarse_setup<R>(ctx, L, B.x, B.gam, B.src, &B.inv, s);
       if (st != NC_OK) return st;

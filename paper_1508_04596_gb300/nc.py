@@ -87,6 +87,9 @@ _SIGS = {
     "nc_sensitivity": (ctypes.c_int, [_ctx, _vp, _vp, _vp, _vp, _vp]),
     "nc_default_opts": (None, [ctypes.POINTER(SolveOpts)]),
     "nc_filter": (ctypes.c_int, [_ctx, _vp, _vp, ctypes.c_double, _vp]),
+    "nc_linearize": (ctypes.c_int, [_ctx, _vp, _vp, _vp]),
+    "nc_jvp_lin": (ctypes.c_int, [_ctx, _vp, _vp, _vp]),
+    "nc_jtvp_lin": (ctypes.c_int, [_ctx, _vp, _vp, _vp]),
     "nc_newton_solve": (ctypes.c_int, [_ctx, _vp, _vp, ctypes.POINTER(SolveOpts),
                                        ctypes.POINTER(SolveInfo), _vp]),
     "nc_adjoint_solve": (ctypes.c_int, [_ctx, _vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts),
@@ -234,6 +237,26 @@ class Problem:
         self._chk(lib.nc_jtvp(self.ctx, self._vec(x, dt, self.ndof, "x"),
                               self._vec(gam, dt, self.E, "gamma"), self._vec(w, dt, self.ndof, "w"),
                               self._vec(out, dt, self.ndof, "JTw"), self._prec(x), _stream(stream)))
+        return out
+
+    def linearize(self, x, gam, stream=None):
+        """Store the linearisation at (x, gamma) (FP64); x and gamma must stay
+        unchanged while jvp_lin / jtvp_lin use it."""
+        self._lin = (x, gam)  # keep the tensors alive
+        self._chk(lib.nc_linearize(self.ctx, self._vec(x, torch.float64, self.ndof, "x"),
+                                   self._vec(gam, torch.float64, self.E, "gamma"),
+                                   _stream(stream)))
+
+    def jvp_lin(self, v, out=None, stream=None):
+        out = torch.empty_like(v) if out is None else out
+        self._chk(lib.nc_jvp_lin(self.ctx, self._vec(v, torch.float64, self.ndof, "v"),
+                                 self._vec(out, torch.float64, self.ndof, "Jv"), _stream(stream)))
+        return out
+
+    def jtvp_lin(self, w, out=None, stream=None):
+        out = torch.empty_like(w) if out is None else out
+        self._chk(lib.nc_jtvp_lin(self.ctx, self._vec(w, torch.float64, self.ndof, "w"),
+                                  self._vec(out, torch.float64, self.ndof, "JTw"), _stream(stream)))
         return out
 
     def diag(self, x, gam, out=None, stream=None):
