@@ -64,6 +64,17 @@ def dist_init(args):
     return rank, world
 
 
+def max_over_ranks(value, device=None):
+    """The largest per-rank value (the slowest rank's step time); one rank: itself."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
     Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
@@ -251,9 +262,7 @@ def run_ours(args, rank, world):
     t_step = float(np.sum(ms)) / args.steps
     if world > 1:
         import torch.distributed as dist
-        tt = torch.tensor([t_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = tt.item()
+        t_step = max_over_ranks(t_step, dev)
         dist.barrier()
     value = world * NAPPLY * ndof / (t_step * 1e-3) / 1e9
 
