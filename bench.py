@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--solve-workload", default=None,
                     help="workload of the state/adjoint design-iteration timing (default: --workload)")
+    ap.add_argument("--vectors-only", default=None, choices=["f32", "f64", "both"],
+                    help="only time the FGMRES orthogonalisation step (the HBM-side kernels) "
+                         "and print its JSON (profiling runs)")
     return ap.parse_args()
 
 
@@ -347,6 +350,7 @@ def run_ours(args, rank, world):
         ops[name] = {"ms": round(t, 4), "gdofs": round(ndof / t / 1e6, 3),
                      "alu_frac": round(FLOPS_PER_ELEM[base] * prob.E / (t * 1e-3) / 1e12 / pk, 4)}
     extra["operators"] = ops
+    extra["hbm_kernels"] = hbm_kernels(prob, stream)
     if solve:
         extra["solve"] = solve
 
@@ -365,6 +369,65 @@ def run_ours(args, rank, world):
             "roofline": roof, "cpu_baseline": cpu}
     line.update(extra)
     return line
+
+
+def hbm_kernels(prob, stream, n=5 * 129 ** 3, k=10, reps=10, only=None):
+    """HBM roofline of the Krylov vector kernels: one FGMRES orthogonalisation
+    step (classical Gram-Schmidt twice, normalisation fused; nc_arnoldi_orth, the
+    routine the solvers run every iteration) of a vector of the 128^3 cavity's
+    size against k = 10 basis columns, FP64 (outer FGMRES) and FP32 (the
+    multigrid smoother's precision).  Algorithmic bytes per call: 4 (k + 1)
+    column reads + 2 writes of n elements.  The basis (0.9 GB in FP64) exceeds
+    L2.  Each call ends with the host read of its k + 1 coefficients, as in
+    FGMRES; that wait is inside the timing."""
+    import torch
+    from paper_1508_04596_gb300 import nc
+    peaks, src = measured_peaks()
+    out = {}
+    for name, dt in (("arnoldi_orth_f64", torch.float64), ("arnoldi_orth_f32", torch.float32)):
+        if only and only not in name:
+            continue
+        ld = nc.mv_ld(n)
+        g = torch.Generator(device="cuda").manual_seed(7)
+        V = torch.zeros(k * ld, dtype=dt, device="cuda")
+        for i in range(k):  # an orthonormal basis, built by the step itself
+            col = torch.randn(n, generator=g, dtype=dt, device="cuda")
+            if i:
+                prob.arnoldi_orth(V, col, i, ld)
+            else:
+                col /= col.norm()
+            V[i * ld:i * ld + n] = col
+        w0 = torch.randn(n, generator=g, dtype=dt, device="cuda")
+        w = w0.clone()
+        for _ in range(2):
+            w.copy_(w0)
+            prob.arnoldi_orth(V, w, k, ld)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t = 0.0
+        for _ in range(reps):
+            w.copy_(w0)
+            a.record(stream)
+            prob.arnoldi_orth(V, w, k, ld)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t += a.elapsed_time(b)
+        t /= reps
+        nbytes = (4 * (k + 1) + 2) * n * w.element_size()
+        gbs = nbytes / (t * 1e-3) / 1e9
+        out[name] = {"ms": round(t, 4), "bytes": int(nbytes), "achieved_gbs": round(gbs, 1),
+                     "peak_gbs": peaks["hbm_gbs"], "frac": round(gbs / peaks["hbm_gbs"], 4),
+                     "peak_source": src, "n": n, "k": k}
+        if dt == torch.float64:
+            # (4k + 1) n FMAs: at 1.25 TFLOP/s FP64 this step is bound by the FP64
+            # pipe (0.70 ms) before HBM (0.58 ms at 6.8 TB/s)
+            tf = 2 * (4 * k + 1) * n / (t * 1e-3) / 1e12
+            out[name].update({"bound": "alu", "achieved_tflops": round(tf, 3),
+                              "alu_peak_tflops": ALU_PEAK_TFLOPS["f64"],
+                              "alu_frac": round(tf / ALU_PEAK_TFLOPS["f64"], 4)})
+        else:
+            out[name]["bound"] = "hbm"
+        del V, w, w0
+    return out
 
 
 # ------------------------------------------------------------------------- CPU oracle
@@ -436,6 +499,13 @@ def run_reference(args, rank, world):
 
 def main():
     args = parse()
+    if args.vectors_only:
+        import torch
+        from paper_1508_04596_gb300 import nc
+        prob = nc.Problem(nc.make_params(2, 2, 2, 0.5, 1e3, 0.71), nc.cavity_bcs())
+        only = None if args.vectors_only == "both" else args.vectors_only
+        print(json.dumps(hbm_kernels(prob, torch.cuda.current_stream(), only=only)))
+        return
     rank, world = dist_init(args)
     line = run_reference(args, rank, world) if args.impl == "reference" else run_ours(args, rank, world)
     if rank == 0 and line is not None:

@@ -246,6 +246,23 @@ void nc_default_opts(nc_solve_opts* opts);
 nc_status nc_newton_solve(nc_ctx* ctx, const double* gamma, double* x_inout,
                           const nc_solve_opts* opts, nc_solve_info* info, void* stream);
 
+/* One orthogonalisation step of the FGMRES Arnoldi process (Sec. 5.2), the
+ * same routine nc_newton_solve and nc_adjoint_solve run every iteration:
+ * classical Gram-Schmidt applied twice against the k orthonormal columns
+ * V_i = V + i*ldv (i < k), each of length n,
+ *   h1 = V^T w,  w1 = w - V h1,  h2 = V^T w1,  w = (w1 - V h2) / nu,
+ * with nu = ||w1 - V h2||, taken as sqrt(||w1||^2 - ||h2||^2) from the second
+ * multi-dot (V orthonormal).  h_host receives k + 1 values: h1 + h2 (the new
+ * Hessenberg column), then nu.  V and w: DEVICE arrays of double (NC_FP64) or
+ * float (NC_FP32); the coefficients are double either way.  ldv >= n; columns
+ * whose start is 16-byte aligned (ldv a multiple of 4 floats / 2 doubles and
+ * an aligned V) take the 16-byte packet path.  A vanishing nu leaves w = w1 - V h2
+ * unscaled.  Uses ctx's reduction scratch only (any context will do).
+ * Synchronous.  NC_ERR_ARG if n < 1, k < 1, k > 64, ldv < n or a pointer is
+ * NULL; NC_ERR_NAN if a coefficient is not finite. */
+nc_status nc_arnoldi_orth(nc_ctx* ctx, long long n, int k, const void* V, long long ldv,
+                          void* w, double* h_host, int prec, void* stream);
+
 /* Adjoint solve J(x, gamma)^T lambda = rhs (Sec. 3.2) by FGMRES + multigrid on the
  * transposed operators, inside FP64 iterative refinement until
  * ||rhs - J^T lambda|| <= rtol_newton ||rhs||.  All FP64 [5][Nn].  Synchronous. */

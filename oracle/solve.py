@@ -98,3 +98,17 @@ def sensitivity(prob, x, gam, lam):
     lam_int = np.where(prob.dmask, 0.0, lam)
     dre = prob.dR_dgamma_elements(x, gam)
     return np.einsum("eaf,eaf->e", gather(lam_int, prob.conn), dre)
+
+
+def gram_schmidt_twice(V, w):
+    """One orthogonalisation step of the FGMRES Arnoldi process (Sec. 5.2), by its
+    plain definition: classical Gram-Schmidt of w against the orthonormal rows
+    of V, applied twice.  V: [k, n], w: [n] (FP64).  Returns (h, nu, q) with
+    h = h1 + h2 the Hessenberg column, nu = ||w - V^T h|| and q the unit vector
+    (w - V^T h) / nu, so that w = V^T h + nu q."""
+    h1 = V @ w
+    w1 = w - V.T @ h1
+    h2 = V @ w1
+    w2 = w1 - V.T @ h2
+    nu = float(np.linalg.norm(w2))
+    return h1 + h2, nu, w2 / nu

@@ -161,14 +161,27 @@ template <typename R>
 void vdiv(long long n, const R* x, const R* d, R* y, cudaStream_t s);  // y = x / d
 template <typename R>
 void vscal(long long n, R a, R* y, cudaStream_t s);  // y = a y
-// out[i] = <X_i, y> for i < k (X_i = X + i*ld); result in device memory (double)
+// Multivectors X_i = X + i*ld are stored with ld = mv_ld(n), a multiple of 64
+// elements, so that every column starts on a 256-byte boundary.
+inline long long mv_ld(long long n) { return (n + 63) / 64 * 64; }
+// out[i] = <X_i, y> for i < k; result in device memory (double)
 template <typename R>
 void vmdot(long long n, int k, const R* X, long long ld, const R* y, double* out, double* partial,
            cudaStream_t s);
-// y -= sum_i coef[i] X_i   (coef in device memory, double)
+// as vmdot, and out[k] = <y, y> from the same pass
+template <typename R>
+void vmdot_self(long long n, int k, const R* X, long long ld, const R* y, double* out,
+                double* partial, cudaStream_t s);
+// y -= sign * sum_i coef[i] X_i   (coef in device memory, double)
 template <typename R>
 void vmaxpy(long long n, int k, const R* X, long long ld, const double* coef, double sign, R* y,
             cudaStream_t s);
+// y <- (y - sum_i h[i] X_i) / nw with nw = sqrt(*q - sum_i h[i]^2) (X orthonormal,
+// *q = ||y||^2 before the update); nw -> *nw_out.  The second pass of classical
+// Gram-Schmidt with its normalisation.
+template <typename R>
+void vmaxpy_scale(long long n, int k, const R* X, long long ld, const double* h, const double* q,
+                  double* nw_out, R* y, cudaStream_t s);
 // y = x * (1/ *nrm) with a breakdown guard (device scalar)
 template <typename R>
 void vscale_inv(long long n, const R* x, const double* nrm, R* y, cudaStream_t s);
@@ -176,18 +189,22 @@ void dev_sqrt_store(const double* in, double* out, cudaStream_t s);
 // *out = ||x||_2
 template <typename R>
 void vnorm(long long n, const R* x, double* out, double* partial, cudaStream_t s);
-// y -= sum_i coef[i] X_i, then *out = ||y||_2
+// Smoother Arnoldi with an unnormalised basis.  vinit_basis: v0 = r (r may be v0
+// itself), t = r / D, *sig2_out = ||r||^2.  varnoldi_update with the dots
+// g[i] = <v_i, w> (i < k) and the squared norms sig2[i]:
+// w <- (w - sum_i g[i]/sig2[i] v_i) / sqrt(sig2[k-1]), t = w / D (t may be null),
+// *sig2_out = ||w||^2.
 template <typename R>
-void vmaxpy_norm(long long n, int k, const R* X, long long ld, const double* coef, R* y,
-                 double* out_norm, double* partial, cudaStream_t s);
-// v = x / *nrm (0 if the norm vanishes), t = v / d
+void vinit_basis(long long n, const R* r, const R* D, R* v0, R* t, double* sig2_out,
+                 double* partial, cudaStream_t s);
 template <typename R>
-void vscale_div(long long n, const R* x, const double* nrm, const R* d, R* v, R* t,
-                cudaStream_t s);
-// z = (sum_i y[i] X_i) / d, or z += ... with accumulate
+void varnoldi_update(long long n, int k, const R* X, long long ld, const double* g,
+                     const double* sig2, const R* D, R* w, R* t, double* sig2_out,
+                     double* partial, cudaStream_t s);
+// z = (sum_i coef[i] X_i) / D (D may be null: no division), or z += ... with accumulate
 template <typename R>
-void vcombine_div(long long n, int k, const R* X, long long ld, const double* y, const R* d, R* z,
-                  bool accumulate, cudaStream_t s);
+void vcombine(long long n, int k, const R* X, long long ld, const double* coef, const R* D, R* z,
+              bool accumulate, cudaStream_t s);
 
 // ---- coarsest-level direct solve (nc_coarse.cu)
 constexpr int COARSE_DENSE_MAX = 1000;  // largest coarsest level solved by a dense inverse

@@ -30,8 +30,8 @@ namespace {
 constexpr int LDH = MAX_RESTART + 1;            // leading dimension of device Hessenbergs
 constexpr int HD_Y = LDH * LDH;                   // y, then g, then the rotations
 constexpr int HD_BETA = HD_Y + 4 * LDH;           // scalar slots
-constexpr int HD_SIZE = HD_BETA + 8;
-constexpr int HD_TMP = HD_BETA + 1;
+constexpr int HD_SIG2 = HD_BETA + 8;              // squared norms of the smoother basis
+constexpr int HD_SIZE = HD_SIG2 + LDH;
 
 template <typename R> LevelBuf<R>& buf(Level& L);
 template <> LevelBuf<double>& buf<double>(Level& L) { return L.f64; }
@@ -46,15 +46,34 @@ nc_status alloc(nc_ctx* ctx, R** p, long long n) {
   return cuda_check(ctx, cudaMalloc((void**)p, sizeof(R) * (size_t)n), "cudaMalloc");
 }
 
-// Least squares  min || beta e1 - H y ||  for a (k+1) x k upper Hessenberg H
-// (column-major, leading dimension LDH, in Hd) by Givens rotations, in place;
-// y -> Hd[HD_Y..].  A vanishing pivot (exhausted Krylov space) gives y = 0 there.
+// Least squares of the smoother's Arnoldi process, on the device.  Column j of
+// Hd holds the raw dots g_ij = <v_i, w_j> (i <= j) of the unnormalised basis
+// v_i (squared norms sig2_i in Hd[HD_SIG2..]), built so that
+//   A D^-1 v_j = sum_i g_ij / sig2_i v_i + sigma_j v_{j+1}.
+// With q_i = v_i / sigma_i this is the usual Arnoldi relation with the
+// Hessenberg entries H_ij = g_ij / (sigma_i sigma_j), H_{j+1,j} = sigma_{j+1},
+// and beta = sigma_0.  Solve min || beta e1 - H y || by Givens rotations (in
+// place), then store the coefficients of the correction on the raw basis,
+// y_j / sigma_j -> Hd[HD_Y + j].  A vanishing norm or pivot (an exhausted
+// Krylov space) contributes zero.
 __global__ void k_small_ls(double* Hd, int k) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double* g = Hd + HD_Y + LDH;  // right-hand side, k + 1 entries
-  const double beta = Hd[HD_BETA];
+  const double* sig2 = Hd + HD_SIG2;
+  auto inv_sig = [&](int i) {
+    const double s2 = sig2[i];
+    return (s2 > 0.0 && s2 < 1e300) ? 1.0 / sqrt(s2) : 0.0;
+  };
+  const double beta = sqrt(fmax(sig2[0], 0.0));
+  Hd[HD_BETA] = beta;
   for (int i = 0; i <= k; ++i) g[i] = 0.0;
   g[0] = (beta > 0.0 && beta < 1e300) ? beta : 0.0;
+  for (int j = 0; j < k; ++j) {  // raw dots -> normalised Hessenberg
+    double* hj = Hd + j * LDH;
+    const double ij = inv_sig(j);
+    for (int i = 0; i <= j; ++i) hj[i] *= inv_sig(i) * ij;
+    hj[j + 1] = (ij > 0.0) ? sqrt(fmax(sig2[j + 1], 0.0)) : 0.0;
+  }
   double rmax = 0.0;
   for (int j = 0; j < k; ++j) {
     double* hj = Hd + j * LDH;
@@ -83,6 +102,7 @@ __global__ void k_small_ls(double* Hd, int k) {
     const double d = Hd[j + j * LDH];
     Hd[HD_Y + j] = (fabs(d) > 1e-14 * rmax && isfinite(acc)) ? acc / d : 0.0;
   }
+  for (int j = 0; j < k; ++j) Hd[HD_Y + j] *= inv_sig(j);
 }
 
 // ------------------------------------------------------------------ level operators
@@ -104,42 +124,44 @@ void level_apply(nc_ctx* ctx, int l, bool tr, const R* v, R* out, cudaStream_t s
 }
 
 // Right Jacobi-preconditioned GMRES(k) on level l:  z += D^-1 V y  approximately
-// solving A z = b.  With zero_init the initial guess is 0.  Per Arnoldi step:
-// the operator on t = v_j / D, one multi-dot, one update-and-norm, and one
-// kernel that normalises v_{j+1} and forms the next t.
+// solving A z = b.  With zero_init the initial guess is 0.  The basis is kept
+// unnormalised (each new vector is divided by the previous vector's norm, so
+// magnitudes stay bounded); k_small_ls turns the raw dots and norms into the
+// normalised Hessenberg.  Per Arnoldi step: the operator on t = D^-1 v_j, one
+// multi-dot, and one pass that orthogonalises, rescales, forms the next t and
+// the new norm.
 template <typename R>
 void smooth(nc_ctx* ctx, int l, bool tr, int k, bool zero_init, cudaStream_t s) {
   Level& L = ctx->lv[l];
   LevelBuf<R>& B = buf<R>(L);
   const long long n = 5 * L.d.Nn;
+  const long long ld = mv_ld(n);
   R* V = B.V;
   double* Hd = B.Hd;
-  const R* r0 = B.b;
-  if (!zero_init) {
+  if (zero_init) {
+    vinit_basis(n, (const R*)B.b, (const R*)B.diag, V, B.t, Hd + HD_SIG2, ctx->partial, s);
+  } else {
     level_apply<R>(ctx, l, tr, B.z, B.t, s);
-    vwaxpy(n, (const R*)B.b, R(-1), (const R*)B.t, B.r, s);
-    r0 = B.r;
+    vwaxpy(n, (const R*)B.b, R(-1), (const R*)B.t, V, s);
+    vinit_basis(n, (const R*)V, (const R*)B.diag, V, B.t, Hd + HD_SIG2, ctx->partial, s);
   }
-  vnorm(n, r0, Hd + HD_BETA, ctx->partial, s);
-  vscale_div(n, r0, Hd + HD_BETA, (const R*)B.diag, V, B.t, s);
   for (int j = 0; j < k; ++j) {
-    R* w = V + (j + 1) * n;
+    R* w = V + (j + 1) * ld;
     level_apply<R>(ctx, l, tr, B.t, w, s);
     double* hcol = Hd + j * LDH;
-    vmdot(n, j + 1, (const R*)V, n, (const R*)w, hcol, ctx->partial, s);
-    vmaxpy_norm(n, j + 1, (const R*)V, n, hcol, w, hcol + j + 1, ctx->partial, s);
-    if (j + 1 < k) vscale_div(n, (const R*)w, hcol + j + 1, (const R*)B.diag, w, B.t, s);
+    vmdot(n, j + 1, (const R*)V, ld, (const R*)w, hcol, ctx->partial, s);
+    varnoldi_update(n, j + 1, (const R*)V, ld, hcol, Hd + HD_SIG2, (const R*)B.diag, w,
+                    j + 1 < k ? B.t : (R*)nullptr, Hd + HD_SIG2 + j + 1, ctx->partial, s);
   }
   k_small_ls<<<1, 1, 0, s>>>(Hd, k);
-  // z (+)= D^-1 (V y); the last basis vector is not needed
-  vcombine_div(n, k, (const R*)V, n, Hd + HD_Y, (const R*)B.diag, B.z, !zero_init, s);
+  // z (+)= D^-1 (V y)
+  vcombine(n, k, (const R*)V, ld, Hd + HD_Y, (const R*)B.diag, B.z, !zero_init, s);
 }
 
 template <typename R>
 void vcycle(nc_ctx* ctx, int l, int nlev, bool tr, const nc_solve_opts& o, cudaStream_t s) {
   Level& L = ctx->lv[l];
   LevelBuf<R>& B = buf<R>(L);
-  const long long n = 5 * L.d.Nn;
   if (l == nlev - 1) {
     if (B.inv)
       coarse_apply<R>(L, tr, B.inv, B.b, B.z, s);
@@ -149,7 +171,7 @@ void vcycle(nc_ctx* ctx, int l, int nlev, bool tr, const nc_solve_opts& o, cudaS
   }
   smooth<R>(ctx, l, tr, o.smooth_its, true, s);
   level_apply<R>(ctx, l, tr, B.z, B.t, s);
-  vwaxpy(n, (const R*)B.b, R(-1), (const R*)B.t, B.r, s);
+  vwaxpy(5 * L.d.Nn, (const R*)B.b, R(-1), (const R*)B.t, B.r, s);
   Level& C = ctx->lv[l + 1];
   op_restrict<R>(L.d, B.r, C.d, buf<R>(C).b, s);
   vcycle<R>(ctx, l + 1, nlev, tr, o, s);
@@ -173,7 +195,7 @@ nc_status alloc_levels(nc_ctx* ctx, int nlev, const nc_solve_opts& o) {
     const long long n = 5 * L.d.Nn;
     const int ks = (l == nlev - 1) ? o.coarse_its : o.smooth_its;
     if (B.V && B.ks < ks) { cudaFree(B.V); B.V = nullptr; }
-    if ((st = alloc(ctx, &B.V, (long long)(ks + 1) * n)) != NC_OK) return st;
+    if ((st = alloc(ctx, &B.V, (long long)(ks + 1) * mv_ld(n))) != NC_OK) return st;
     if (B.ks < ks) B.ks = ks;
     if ((st = alloc(ctx, &B.diag, n)) != NC_OK || (st = alloc(ctx, &B.b, n)) != NC_OK ||
         (st = alloc(ctx, &B.z, n)) != NC_OK || (st = alloc(ctx, &B.r, n)) != NC_OK ||
@@ -333,12 +355,30 @@ nc_status norm2(nc_ctx* ctx, long long n, const double* v, double* out, cudaStre
   return NC_OK;
 }
 
+// Classical Gram-Schmidt applied twice to w against the k orthonormal columns
+// X_i = X + i*ld, with the normalisation folded into the second update: the
+// second multi-dot also gives ||w1||^2, and ||w1 - X h2||^2 = ||w1||^2 - ||h2||^2
+// (X orthonormal).  Device results: hc[0..k) = h1, hc[off..off+k) = h2,
+// hc[off+k] = ||w1||^2, hc[2 off] = the final norm.  Four passes over the
+// columns instead of six (two multi-dots, two updates, a norm and a scaling).
+template <typename R>
+void cgs2(long long n, int k, const R* X, long long ld, R* w, double* hc, int off,
+          double* partial, cudaStream_t s) {
+  double* h1 = hc;
+  double* h2 = hc + off;
+  vmdot(n, k, X, ld, (const R*)w, h1, partial, s);
+  vmaxpy(n, k, X, ld, h1, 1.0, w, s);
+  vmdot_self(n, k, X, ld, (const R*)w, h2, partial, s);
+  vmaxpy_scale(n, k, X, ld, h2, h2 + k, hc + 2 * off, w, s);
+}
+
 // Solve A x = b to ||b - A x|| <= rtol ||b|| (x starts at 0).  its += iterations.
 nc_status fgmres(nc_ctx* ctx, const LinSolve& ls, const nc_solve_opts& o, const double* b, double* x,
                  double rtol, int* its, cudaStream_t s) {
   Level& L = ctx->lv[0];
   const long long n = 5 * L.d.Nn;
   const int m = ctx->kry.m;
+  const long long ld = mv_ld(n);
   double* V = ctx->kry.V;
   double* Z = ctx->kry.Z;
   double* hc = ctx->kry.hcol;
@@ -369,25 +409,19 @@ nc_status fgmres(nc_ctx* ctx, const LinSolve& ls, const nc_solve_opts& o, const 
     int j = 0;
     bool done = false;
     for (; j < m && total < o.max_lin; ++j) {
-      double* vj = V + j * n;
-      double* zj = Z + j * n;
-      double* w = V + (j + 1) * n;
+      double* vj = V + j * ld;
+      double* zj = Z + j * ld;
+      double* w = V + (j + 1) * ld;
       precond(ctx, ls, o, graph, vj, zj, s);
       apply_A(ctx, ls, zj, w, s);
-      // classical Gram-Schmidt, twice
-      vmdot(n, j + 1, (const double*)V, n, (const double*)w, hc, ctx->partial, s);
-      vmaxpy(n, j + 1, (const double*)V, n, hc, 1.0, w, s);
-      vmdot(n, j + 1, (const double*)V, n, (const double*)w, hc + (m + 2), ctx->partial, s);
-      vmaxpy(n, j + 1, (const double*)V, n, hc + (m + 2), 1.0, w, s);
-      vmdot(n, 1, (const double*)w, 0, (const double*)w, hc + 2 * (m + 2), ctx->partial, s);
-      // one device-to-host read per iteration: both Gram-Schmidt columns and ||w||^2
+      cgs2(n, j + 1, (const double*)V, ld, w, hc, m + 2, ctx->partial, s);
+      // one device-to-host read per iteration: both Gram-Schmidt columns and ||w||
       if ((st = read_scalar(ctx, hc, hh.data(), 2 * (m + 2) + 1, s)) != NC_OK) return st;
-      const double nw2 = hh[2 * (m + 2)];
-      if (!std::isfinite(nw2)) return set_err(ctx, NC_ERR_NAN, "non-finite value in FGMRES");
-      const double nw = std::sqrt(std::fmax(nw2, 0.0));
+      const double nw = hh[2 * (m + 2)];
+      if (!std::isfinite(nw) || !std::isfinite(hh[(m + 2) + j + 1]))
+        return set_err(ctx, NC_ERR_NAN, "non-finite value in FGMRES");
       for (int i = 0; i <= j; ++i) H[i + (size_t)j * (m + 1)] = hh[i] + hh[(m + 2) + i];
       H[j + 1 + (size_t)j * (m + 1)] = nw;
-      if (nw > 0.0) vscal(n, 1.0 / nw, w, s);
       // apply previous rotations, then a new one
       for (int i = 0; i < j; ++i) {
         const double t1 = H[i + (size_t)j * (m + 1)], t2 = H[i + 1 + (size_t)j * (m + 1)];
@@ -421,7 +455,7 @@ nc_status fgmres(nc_ctx* ctx, const LinSolve& ls, const nc_solve_opts& o, const 
       if ((st = cuda_check(ctx, cudaMemcpyAsync(ctx->kry.y, y.data(), sizeof(double) * j,
                                                 cudaMemcpyHostToDevice, s), "upload y")) != NC_OK)
         return st;
-      vmaxpy(n, j, (const double*)Z, n, ctx->kry.y, -1.0, x, s);
+      vmaxpy(n, j, (const double*)Z, ld, ctx->kry.y, -1.0, x, s);
       if ((st = cuda_check(ctx, cudaStreamSynchronize(s), "fgmres sync")) != NC_OK) return st;
     }
     first = false;
@@ -455,8 +489,8 @@ nc_status prepare(nc_ctx* ctx, const nc_solve_opts& o, int nlev, bool mixed) {
     ctx->kry.m = 0;
   }
   if (!ctx->kry.V) {
-    if ((st = alloc(ctx, &ctx->kry.V, (long long)(o.restart + 1) * n)) != NC_OK ||
-        (st = alloc(ctx, &ctx->kry.Z, (long long)o.restart * n)) != NC_OK)
+    if ((st = alloc(ctx, &ctx->kry.V, (long long)(o.restart + 1) * mv_ld(n))) != NC_OK ||
+        (st = alloc(ctx, &ctx->kry.Z, (long long)o.restart * mv_ld(n))) != NC_OK)
       return st;
     ctx->kry.m = o.restart;
   }
@@ -671,6 +705,30 @@ nc_status nc_newton_solve(nc_ctx* ctx, const double* gam, double* x, const nc_so
   return st;
 }
 
+nc_status nc_arnoldi_orth(nc_ctx* ctx, long long n, int k, const void* V, long long ldv, void* w,
+                          double* h_host, int prec, void* stream) {
+  if (!ctx) return NC_ERR_ARG;
+  if (!V || !w || !h_host || n < 1 || k < 1 || k > MAX_RESTART || ldv < n ||
+      (prec != NC_FP64 && prec != NC_FP32))
+    return set_err(ctx, NC_ERR_ARG, "nc_arnoldi_orth: invalid argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int off = MAX_RESTART + 2;
+  double* hc = ctx->dscal;  // 2 * off + 1 slots
+  if (prec == NC_FP64)
+    cgs2(n, k, (const double*)V, ldv, (double*)w, hc, off, ctx->partial, s);
+  else
+    cgs2(n, k, (const float*)V, ldv, (float*)w, hc, off, ctx->partial, s);
+  std::vector<double> hh(2 * off + 1);
+  nc_status st = read_scalar(ctx, hc, hh.data(), 2 * off + 1, s);
+  if (st != NC_OK) return st;
+  for (int i = 0; i < k; ++i) h_host[i] = hh[i] + hh[off + i];
+  h_host[k] = hh[2 * off];
+  for (int i = 0; i <= k; ++i)
+    if (!std::isfinite(h_host[i]) || !std::isfinite(hh[off + k]))
+      return set_err(ctx, NC_ERR_NAN, "nc_arnoldi_orth: non-finite coefficient");
+  return NC_OK;
+}
+
 nc_status nc_adjoint_solve(nc_ctx* ctx, const double* x, const double* gam, const double* rhs,
                            double* lam, const nc_solve_opts* opts, nc_solve_info* info_out,
                            void* stream) {
@@ -700,15 +758,20 @@ nc_status nc_adjoint_solve(nc_ctx* ctx, const double* x, const double* gam, cons
     const LinSolve ls{true, mixed, nlev};
     int k = 0;
     double nr = nb;
+    // the state and the design do not change during the refinement: one
+    // linearisation of every level serves all sweeps
+    bool linearized = false;
     while (st == NC_OK && nr > o.rtol_newton * nb && nr > 0.0) {
       if (k >= o.max_newton) { st = set_err(ctx, NC_ERR_MAXIT, "adjoint refinement limit"); break; }
-      st = mixed ? linearize<float>(ctx, nlev, x, gam, s) : linearize<double>(ctx, nlev, x, gam, s);
-      if (st != NC_OK) break;
+      if (!linearized) {
+        st = mixed ? linearize<float>(ctx, nlev, x, gam, s) : linearize<double>(ctx, nlev, x, gam, s);
+        if (st != NC_OK) break;
+        linearized = true;
+      }
       int lits = 0;
       // inner relative tolerance: no tighter than needed for the outer target
       const double rt = std::fmax(o.rtol_lin, 0.5 * o.rtol_newton * nb / nr);
       st = fgmres(ctx, ls, o, r, dl, std::fmin(rt, 0.5), &lits, s);
-      release_ext(ctx);
       info.lin_its_total += lits;
       if (st != NC_OK && st != NC_ERR_MAXIT) break;
       vaxpy(n, 1.0, (const double*)dl, lam, s);

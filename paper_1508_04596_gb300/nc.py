@@ -94,6 +94,9 @@ _SIGS = {
                                        ctypes.POINTER(SolveInfo), _vp]),
     "nc_adjoint_solve": (ctypes.c_int, [_ctx, _vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts),
                                         ctypes.POINTER(SolveInfo), _vp]),
+    "nc_arnoldi_orth": (ctypes.c_int, [_ctx, ctypes.c_longlong, ctypes.c_int, _vp,
+                                       ctypes.c_longlong, _vp, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.c_int, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -153,6 +156,12 @@ def make_params(nx, ny, nz, h, Gr, Pr, alpha_max=1e4, q_alpha=1.0, q_f=1.0, Ck=0
     p.alpha_max, p.q_alpha, p.q_f, p.Ck = alpha_max, q_alpha, q_f, Ck
     p.g_dir[:] = list(g_dir)
     return p
+
+
+def mv_ld(n):
+    """Column stride the solvers use for multivectors of length n (a multiple of
+    64 elements, so that every column starts on a 256-byte boundary)."""
+    return (n + 63) // 64 * 64
 
 
 def _stream(stream):
@@ -238,6 +247,22 @@ class Problem:
                               self._vec(gam, dt, self.E, "gamma"), self._vec(w, dt, self.ndof, "w"),
                               self._vec(out, dt, self.ndof, "JTw"), self._prec(x), _stream(stream)))
         return out
+
+    def arnoldi_orth(self, V, w, k, ldv, stream=None):
+        """One FGMRES orthogonalisation step (classical Gram-Schmidt twice) of w
+        against the k orthonormal columns V[i*ldv : i*ldv + n], n = w.numel();
+        w is overwritten by the new unit basis vector.  Returns the k + 1
+        coefficients (the Hessenberg column, then the norm) as a list."""
+        n = w.numel()
+        if not (isinstance(V, torch.Tensor) and V.is_cuda and V.dtype == w.dtype
+                and V.is_contiguous() and V.numel() >= (k - 1) * ldv + n):
+            raise ValueError("V must be a contiguous CUDA tensor of w's dtype holding k columns")
+        self._vec(w, w.dtype, n, "w")
+        h = (ctypes.c_double * (k + 1))()
+        self._chk(lib.nc_arnoldi_orth(self.ctx, n, k, ctypes.c_void_p(V.data_ptr()), ldv,
+                                      ctypes.c_void_p(w.data_ptr()), h, self._prec(w),
+                                      _stream(stream)))
+        return list(h)
 
     def linearize(self, x, gam, stream=None):
         """Store the linearisation at (x, gamma) (FP64); x and gamma must stay

@@ -147,13 +147,17 @@ def test_autograd_filtered_design(nc):
 
 
 def test_mixed_matches_fp64_32(nc):
-    """32^3 cavity at Gr = 1e5: the mixed-precision Newton state and adjoint
-    agree with the plain FP64 ones to <= 1e-8 relative."""
+    """32^3 cavity at Gr = 1e5: the mixed-precision Newton state agrees with the
+    plain FP64 one to <= 1e-8 relative (Newton's quadratic convergence puts the
+    state far inside its 1e-8 residual tolerance), and both adjoint solves meet
+    their 1e-8 residual tolerance.  The adjoint stops on the residual, which
+    bounds the solution error only by cond(J) x 1e-8, so the two adjoint
+    solutions are compared after solving both to 1e-11: <= 1e-8 relative."""
     n = 32
     p = nc.make_params(n, n, n, 1.0 / n, 1e5, 0.71, **synth.MATERIAL)
     prob = nc.Problem(p, nc.cavity_bcs(nc.PATCH_FLUX, 1.0))
     gam = dev(synth.smoothed_random(n, n, n, 1.0 / n, 8))
-    xs, ls = [], []
+    xs = []
     for mixed in (1, 0):
         opts = nc.default_opts(mixed=mixed, ramp_steps=3)
         x = torch.zeros(prob.ndof, dtype=torch.float64, device="cuda")
@@ -161,11 +165,13 @@ def test_mixed_matches_fp64_32(nc):
         assert info["status"] == "NC_OK"
         phi, dphi = prob.objective(x)
         lam, ainfo = prob.adjoint_solve(x, gam, -dphi, opts=opts)
-        assert ainfo["status"] == "NC_OK"
+        assert ainfo["status"] == "NC_OK" and ainfo["res_final"] <= 1e-8 * ainfo["res0"]
         xs.append(x)
-        ls.append(lam)
     assert (torch.linalg.norm(xs[0] - xs[1]) / torch.linalg.norm(xs[1])).item() <= 1e-8
-    assert (torch.linalg.norm(ls[0] - ls[1]) / torch.linalg.norm(ls[1])).item() <= 1e-7
+    _, dphi = prob.objective(xs[1])
+    ls = [prob.adjoint_solve(xs[1], gam, -dphi, opts=nc.default_opts(mixed=m, rtol_newton=1e-11))[0]
+          for m in (1, 0)]
+    assert (torch.linalg.norm(ls[0] - ls[1]) / torch.linalg.norm(ls[1])).item() <= 1e-8
 
 
 def test_newton_ramping_recovers(nc):

@@ -488,3 +488,22 @@ def test_adjoint_dot_product():
     J = prob.jacobian(x, gam)
     v, w = rng.standard_normal(g.ndof), rng.standard_normal(g.ndof)
     assert w @ (J @ v) == pytest.approx(v @ (J.T @ w), rel=1e-13)
+
+
+def test_gram_schmidt_step_against_least_squares():
+    """Arnoldi orthogonalisation (Sec. 5.2): for orthonormal V the step returns
+    h = V w, nu = the distance from w to span(V) (a least-squares residual from
+    numpy's lstsq) and a unit q orthogonal to V with w = V^T h + nu q; a
+    nearly dependent w (1e-6 off the span) keeps q orthogonal to V."""
+    rng = np.random.default_rng(11)
+    n, k = 257, 7
+    V = np.linalg.qr(rng.standard_normal((n, k)))[0].T
+    for off in (1.0, 1e-6):
+        w = V.T @ rng.standard_normal(k) + off * rng.standard_normal(n)
+        h, nu, q = S.gram_schmidt_twice(V, w)
+        coef, res, _, _ = np.linalg.lstsq(V.T, w, rcond=None)
+        assert np.allclose(h, coef, rtol=0, atol=1e-13 * np.linalg.norm(w))
+        assert abs(nu - np.sqrt(res[0])) <= 1e-9 * nu
+        assert abs(np.linalg.norm(q) - 1.0) <= 1e-14
+        assert np.max(np.abs(V @ q)) <= 1e-14
+        assert np.linalg.norm(V.T @ h + nu * q - w) <= 1e-13 * np.linalg.norm(w)
