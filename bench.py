@@ -32,8 +32,8 @@ NAPPLY = 16  # J v applications per step
 # Operation counts per element (one +, -, * or / = 1 flop; an FMA = 2), of the
 # element routines in csrc/nc_element.cuh, counted by instantiating them with a
 # counting number type.
-FLOPS_PER_ELEM = {"residual": 3038, "jvp": 4950, "jtvp": 4718, "diag": 7293, "sens": 4282,
-                  "linearize": 1266, "jvp_lin": 3698}
+FLOPS_PER_ELEM = {"residual": 2633, "jvp": 4345, "jtvp": 4466, "diag": 7272, "sens": 3797,
+                  "linearize": 1245, "jvp_lin": 3117}
 # ALU peaks (whole GPU): FP32 = 152 SM x 128 lanes x 2 flop x 2.07 GHz; FP64 = the
 # GB300's nominal 1.25 TFLOP/s (equal to our FMA-chain probe on the box: 78.5 and
 # 1.25 TFLOP/s measured).

@@ -37,8 +37,11 @@ template <typename R>
 struct ElemConst {
   R inv_h;      // 1/h
   R wq;         // Gauss weight (h/2)^3
+  R wh;         // wq / h: weight of the gradient-slot fluxes F1
   R Pr, beta;   // Pr, Gr Pr^2
   R eg[3];      // unit gravity direction
+  R beg[3];     // beta * eg
+  R prw, prw2;  // Pr wh, 2 Pr wh
   R inv16h2;    // 1/(4h)^2      : tau1^-2 = S * inv16h2
   R t2inv2;     // (4 Pr/h^2)^2  : tau2^-2
   R k2c;        // (4/h^2)^2     : (h^2/(4K))^-2 = K^2 * k2c
@@ -220,11 +223,20 @@ NC_HD void test_all_pair(R out[5][8], R cy, R cz, const R f0[2][5], const R F1[2
   }
 }
 
-// Element coefficients shared by all Gauss points.
+// Element coefficients shared by all Gauss points; wtau, wtauT, wK are tau,
+// tau_T and K times the F1 weight wh.
 template <typename R>
 struct ElemCoef {
   R alpha, K, tau, tauT, s;
+  R wtau, wtauT, wK;
 };
+
+template <typename R>
+NC_HD void scale_coef(ElemCoef<R>& k, const ElemConst<R>& c) {
+  k.wtau = c.wh * k.tau;
+  k.wtauT = c.wh * k.tauT;
+  k.wK = c.wh * k.K;
+}
 
 template <typename R>
 NC_HD ElemCoef<R> elem_coef(const R xe[5][8], R gam, R s, const ElemConst<R>& c, R& S) {
@@ -240,19 +252,41 @@ NC_HD ElemCoef<R> elem_coef(const R xe[5][8], R gam, R s, const ElemConst<R>& c,
   k.tau = nc_rsqrt(S * c.inv16h2 + c.t2inv2 + k.alpha * k.alpha);
   k.tauT = nc_rsqrt(S * c.inv16h2 + k.K * k.K * c.k2c);
   k.s = s;
+  scale_coef(k, c);
   return k;
 }
 
-// Strong residuals at a quadrature point.
+// Strong residuals at a quadrature point; body = rM without the pressure
+// gradient (convection, Brinkman friction and buoyancy), the value-slot flux of
+// the momentum rows.
 template <typename R>
-NC_HD void strong(const QP<R>& q, const ElemCoef<R>& k, const ElemConst<R>& c, R conv[3],
+NC_HD void strong(const QP<R>& q, const ElemCoef<R>& k, const ElemConst<R>& c, R body[3],
                   R rM[3], R& rT) {
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    conv[i] = q.u[0] * q.G[i][0] + q.u[1] * q.G[i][1] + q.u[2] * q.G[i][2];
-    rM[i] = conv[i] + q.gp[i] + k.alpha * q.u[i] + c.beta * c.eg[i] * q.T;
+    body[i] = q.u[0] * q.G[i][0] + q.u[1] * q.G[i][1] + q.u[2] * q.G[i][2] + k.alpha * q.u[i] +
+              c.beg[i] * q.T;
+    rM[i] = body[i] + q.gp[i];
   }
   rT = q.u[0] * q.gT[0] + q.u[1] * q.gT[1] + q.u[2] * q.gT[2] - k.s;
+}
+
+// Gradient-slot momentum fluxes shared by the residual and its tangent:
+// F1[i][j] = Pr wh (G_ij + G_ji) - delta_ij pw + u_j a_i (+ v_j b_i with HASV; the
+// viscous part formed once per symmetric pair).
+template <typename R, bool HASV>
+NC_HD void momentum_F1(const R G[3][3], R pw, const R u[3], const R a[3], const R v[3],
+                       const R b[3], const ElemConst<R>& c, R F1[5][3]) {
+  const R v01 = c.prw * (G[0][1] + G[1][0]);
+  const R v02 = c.prw * (G[0][2] + G[2][0]);
+  const R v12 = c.prw * (G[1][2] + G[2][1]);
+  const R vd[3] = {c.prw2 * G[0][0] - pw, c.prw2 * G[1][1] - pw, c.prw2 * G[2][2] - pw};
+  const R vo[3][3] = {{vd[0], v01, v02}, {v01, vd[1], v12}, {v02, v12, vd[2]}};
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      F1[i][j] = HASV ? vo[i][j] + u[j] * a[i] + v[j] * b[i] : vo[i][j] + u[j] * a[i];
 }
 
 // ---------------------------------------------------------------------------- residual
@@ -260,24 +294,22 @@ NC_HD void strong(const QP<R>& q, const ElemCoef<R>& k, const ElemConst<R>& c, R
 template <typename R>
 NC_HD void flux_residual(const QP<R>& q, const ElemCoef<R>& k, const ElemConst<R>& c, R f0[5],
                          R F1[5][3]) {
-  R conv[3], rM[3], rT;
-  strong(q, k, c, conv, rM, rT);
-  const R w = c.wq, wh = c.wq * c.inv_h;
+  R body[3], rM[3], rT;
+  strong(q, k, c, body, rM, rT);
+  const R w = c.wq;
+  R b[3];  // wh tau rM: the SUPG weight of the momentum rows and the PSPG flux
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const R trM = k.tau * rM[i];
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      F1[i][j] = wh * (c.Pr * (q.G[i][j] + q.G[j][i]) - (i == j ? q.p : R(0)) + q.u[j] * trM);
-    f0[i] = w * (conv[i] + k.alpha * q.u[i] + c.beta * c.eg[i] * q.T);
+    b[i] = k.wtau * rM[i];
+    f0[i] = w * body[i];
+    F1[3][i] = b[i];
   }
+  momentum_F1<R, false>(q.G, c.wh * q.p, q.u, b, q.u, b, c, F1);
   f0[3] = w * (q.G[0][0] + q.G[1][1] + q.G[2][2]);
-#pragma unroll
-  for (int j = 0; j < 3; ++j) F1[3][j] = wh * k.tau * rM[j];
   f0[4] = w * rT;
-  const R trT = k.tauT * rT;
+  const R trT = k.wtauT * rT;
 #pragma unroll
-  for (int j = 0; j < 3; ++j) F1[4][j] = wh * (k.K * q.gT[j] + q.u[j] * trT);
+  for (int j = 0; j < 3; ++j) F1[4][j] = k.wK * q.gT[j] + q.u[j] * trT;
 }
 
 template <typename R>
@@ -328,50 +360,50 @@ NC_HD void elem_residual(const R xe[5][8], R gam, R s, const ElemConst<R>& c, R 
 }
 
 // ---------------------------------------------------------------------------- tangent
-// Directional derivative of the pointwise fluxes in the state direction d and
-// the parameter directions (dalpha, dK, dtau, dtauT); returns w-scaled f0 and
-// (w/h)-scaled F1.
-template <typename R>
+// Directional derivative of the pointwise fluxes in the state direction d and,
+// with PARAM, the parameter directions (dalpha, dK); dtau, dtauT are the
+// derivatives of tau, tau_T along the same direction.  Returns w-scaled f0 and
+// (w/h)-scaled F1.  Without PARAM, dalpha and dK are not read (J v needs none).
+template <typename R, bool PARAM>
 NC_HD void flux_tangent_rm(const QP<R>& q, const R rM[3], R rT, const QP<R>& d,
                            const ElemCoef<R>& k, R dalpha, R dK, R dtau, R dtauT,
                            const ElemConst<R>& c, R f0[5], R F1[5][3]) {
-  R dconv[3], drM[3];
+  const R w = c.wq;
+  const R whdtau = c.wh * dtau;
+  R a[3], b[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    dconv[i] = d.u[0] * q.G[i][0] + d.u[1] * q.G[i][1] + d.u[2] * q.G[i][2] +
-               q.u[0] * d.G[i][0] + q.u[1] * d.G[i][1] + q.u[2] * d.G[i][2];
-    drM[i] = dconv[i] + d.gp[i] + k.alpha * d.u[i] + dalpha * q.u[i] + c.beta * c.eg[i] * d.T;
+    // derivative of rM_i without the pressure gradient (the value-slot flux)
+    R body = d.u[0] * q.G[i][0] + d.u[1] * q.G[i][1] + d.u[2] * q.G[i][2] + q.u[0] * d.G[i][0] +
+             q.u[1] * d.G[i][1] + q.u[2] * d.G[i][2] + k.alpha * d.u[i] + c.beg[i] * d.T;
+    if (PARAM) body += dalpha * q.u[i];
+    const R drM = body + d.gp[i];
+    f0[i] = w * body;
+    // d(tau u_j rM_i) = u_j (dtau rM_i + tau drM_i) + d.u_j (tau rM_i), times wh
+    a[i] = whdtau * rM[i] + k.wtau * drM;
+    b[i] = k.wtau * rM[i];
+    F1[3][i] = a[i];
   }
-  const R drT = d.u[0] * q.gT[0] + d.u[1] * q.gT[1] + d.u[2] * q.gT[2] +
-                q.u[0] * d.gT[0] + q.u[1] * d.gT[1] + q.u[2] * d.gT[2];
-  const R w = c.wq, wh = c.wq * c.inv_h;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    f0[i] = w * (dconv[i] + k.alpha * d.u[i] + dalpha * q.u[i] + c.beta * c.eg[i] * d.T);
-    // d(tau u_j rM_i) = u_j (dtau rM_i + tau drM_i) + d.u_j (tau rM_i)
-    const R a = dtau * rM[i] + k.tau * drM[i];
-    const R b = k.tau * rM[i];
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      F1[i][j] = wh * (c.Pr * (d.G[i][j] + d.G[j][i]) - (i == j ? d.p : R(0)) + q.u[j] * a +
-                       d.u[j] * b);
-  }
+  momentum_F1<R, true>(d.G, c.wh * d.p, q.u, a, d.u, b, c, F1);
+  const R drT = d.u[0] * q.gT[0] + d.u[1] * q.gT[1] + d.u[2] * q.gT[2] + q.u[0] * d.gT[0] +
+                q.u[1] * d.gT[1] + q.u[2] * d.gT[2];
   f0[3] = w * (d.G[0][0] + d.G[1][1] + d.G[2][2]);
-#pragma unroll
-  for (int j = 0; j < 3; ++j) F1[3][j] = wh * (dtau * rM[j] + k.tau * drM[j]);
   f0[4] = w * drT;
-  const R aT = dtauT * rT + k.tauT * drT, bT = k.tauT * rT;
+  const R aT = (c.wh * dtauT) * rT + k.wtauT * drT, bT = k.wtauT * rT;
 #pragma unroll
-  for (int j = 0; j < 3; ++j)
-    F1[4][j] = wh * (k.K * d.gT[j] + dK * q.gT[j] + q.u[j] * aT + d.u[j] * bT);
+  for (int j = 0; j < 3; ++j) {
+    R t = k.wK * d.gT[j] + q.u[j] * aT + d.u[j] * bT;
+    if (PARAM) t += (c.wh * dK) * q.gT[j];
+    F1[4][j] = t;
+  }
 }
 
-template <typename R>
+template <typename R, bool PARAM>
 NC_HD void flux_tangent(const QP<R>& q, const QP<R>& d, const ElemCoef<R>& k, R dalpha, R dK,
                         R dtau, R dtauT, const ElemConst<R>& c, R f0[5], R F1[5][3]) {
-  R conv[3], rM[3], rT;
-  strong(q, k, c, conv, rM, rT);
-  flux_tangent_rm(q, rM, rT, d, k, dalpha, dK, dtau, dtauT, c, f0, F1);
+  R body[3], rM[3], rT;
+  strong(q, k, c, body, rM, rT);
+  flux_tangent_rm<R, PARAM>(q, rM, rT, d, k, dalpha, dK, dtau, dtauT, c, f0, F1);
 }
 
 template <typename R>
@@ -381,8 +413,8 @@ NC_HD void pair_jvp(const R xe[5][8], const R ve[5][8], const ElemCoef<R>& k, R 
   interp_all_pair<R>(xe, c.inv_h, cy, cz, q);
   interp_all_pair<R>(ve, c.inv_h, cy, cz, d);
   R f0[2][5], F1[2][5][3];
-  flux_tangent(q[0], d[0], k, R(0), R(0), dtau, dtauT, c, f0[0], F1[0]);
-  flux_tangent(q[1], d[1], k, R(0), R(0), dtau, dtauT, c, f0[1], F1[1]);
+  flux_tangent<R, false>(q[0], d[0], k, R(0), R(0), dtau, dtauT, c, f0[0], F1[0]);
+  flux_tangent<R, false>(q[1], d[1], k, R(0), R(0), dtau, dtauT, c, f0[1], F1[1]);
   test_all_pair<R>(out, cy, cz, f0, F1);
 }
 
@@ -408,31 +440,26 @@ NC_HD void elem_jvp(const R xe[5][8], const R ve[5][8], R gam, R s, const ElemCo
 // Given the interpolated test field t (value and gradient per field at the
 // point), the cotangents of the point state, (dFlux/dq)^T (w t), returned as
 // f0 (value slots) and F1 (gradient slots, times 1/h) for the test-side
-// transpose, plus the cotangents of tau and tau_T accumulated.
+// transpose, plus the cotangents of tau and tau_T accumulated WITHOUT the Gauss
+// weight w (the caller applies it once per element).  The weight is applied to
+// the 20 outputs rather than to the 20 seeds, and the symmetric viscous
+// cotangent is formed once per pair (i, j).
 template <typename R>
 NC_HD void flux_adjoint_rm(const QP<R>& q, const R rM[3], R rT, const QP<R>& t,
                            const ElemCoef<R>& k, const ElemConst<R>& c, R f0[5], R F1[5][3],
                            R& tau_bar, R& tauT_bar) {
-  const R w = c.wq;
-  R c0[5] = {w * t.u[0], w * t.u[1], w * t.u[2], w * t.p, w * t.T};
-  R C1[5][3];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    C1[0][j] = w * t.G[0][j];
-    C1[1][j] = w * t.G[1][j];
-    C1[2][j] = w * t.G[2][j];
-    C1[3][j] = w * t.gp[j];
-    C1[4][j] = w * t.gT[j];
-  }
+  // seeds: c0 = test values, C1 = test gradients (unweighted)
+  const R* const C1[5] = {t.G[0], t.G[1], t.G[2], t.gp, t.gT};
+  const R c0[5] = {t.u[0], t.u[1], t.u[2], t.p, t.T};
   R rMb[3], ub[3], Gb[3][3], gTb[3];
   const R C4u = C1[4][0] * q.u[0] + C1[4][1] * q.u[1] + C1[4][2] * q.u[2];
   const R rTb = c0[4] + k.tauT * C4u;
   R tb = R(0);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const R Ciu = C1[i][0] * q.u[0] + C1[i][1] * q.u[1] + C1[i][2] * q.u[2];
-    rMb[i] = k.tau * (Ciu + C1[3][i]);
-    tb += (Ciu + C1[3][i]) * rM[i];
+    const R s = C1[i][0] * q.u[0] + C1[i][1] * q.u[1] + C1[i][2] * q.u[2] + C1[3][i];
+    rMb[i] = k.tau * s;
+    tb += s * rM[i];
   }
   tau_bar += tb;
   tauT_bar += C4u * rT;
@@ -445,38 +472,40 @@ NC_HD void flux_adjoint_rm(const QP<R>& q, const R rM[3], R rT, const QP<R>& t,
             rTb * q.gT[j];
     gTb[j] = k.K * C1[4][j] + rTb * q.u[j];
   }
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) Gb[i][j] = c.Pr * (C1[i][j] + C1[j][i]);
+  {
+    const R g01 = c.Pr * (C1[0][1] + C1[1][0]), g02 = c.Pr * (C1[0][2] + C1[2][0]);
+    const R g12 = c.Pr * (C1[1][2] + C1[2][1]);
+    const R p2 = R(2) * c.Pr;
+    Gb[0][0] = p2 * C1[0][0] + c0[3];
+    Gb[1][1] = p2 * C1[1][1] + c0[3];
+    Gb[2][2] = p2 * C1[2][2] + c0[3];
+    Gb[0][1] = Gb[1][0] = g01;
+    Gb[0][2] = Gb[2][0] = g02;
+    Gb[1][2] = Gb[2][1] = g12;
+  }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const R cb = c0[i] + rMb[i];  // cotangent of conv_i (and of the body terms)
     ub[i] += k.alpha * cb;
-    Tb += c.beta * c.eg[i] * cb;
-    Gb[i][i] += c0[3];
+    Tb += c.beg[i] * cb;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       ub[j] += cb * q.G[i][j];
       Gb[i][j] += cb * q.u[j];
     }
   }
-  const R ih = c.inv_h;
+  const R w = c.wq, wh = c.wh;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    f0[i] = ub[i];
-    F1[i][0] = Gb[i][0] * ih;
-    F1[i][1] = Gb[i][1] * ih;
-    F1[i][2] = Gb[i][2] * ih;
+    f0[i] = w * ub[i];
+    F1[i][0] = wh * Gb[i][0];
+    F1[i][1] = wh * Gb[i][1];
+    F1[i][2] = wh * Gb[i][2];
+    F1[3][i] = wh * rMb[i];
+    F1[4][i] = wh * gTb[i];
   }
-  f0[3] = pb;
-  F1[3][0] = rMb[0] * ih;
-  F1[3][1] = rMb[1] * ih;
-  F1[3][2] = rMb[2] * ih;
-  f0[4] = Tb;
-  F1[4][0] = gTb[0] * ih;
-  F1[4][1] = gTb[1] * ih;
-  F1[4][2] = gTb[2] * ih;
+  f0[3] = w * pb;
+  f0[4] = w * Tb;
 }
 
 template <typename R>
@@ -509,7 +538,7 @@ NC_HD void elem_jtvp(const R xe[5][8], const R we[5][8], R gam, R s, const ElemC
   R tb = R(0), tbT = R(0);
   NC_FOR_PAIRS(pair_jtvp<R>(xe, we, k, c, cy, cz, out, tb, tbT))
   // tau(S), S = u_e^T u_e:  d tau/d u_e = -tau^3/(16 h^2) u_e  (App. B)
-  const R gsum = -(k.tau * k.tau * k.tau * tb + k.tauT * k.tauT * k.tauT * tbT) * c.inv16h2;
+  const R gsum = -(k.tau * k.tau * k.tau * tb + k.tauT * k.tauT * k.tauT * tbT) * (c.wq * c.inv16h2);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -529,7 +558,7 @@ NC_HD R point_sens(const QP<R>& q, const QP<R>& t, const ElemCoef<R>& k, R dalph
     for (int j = 0; j < 3; ++j) zero.G[i][j] = R(0);
   }
   R f0[5], F1[5][3];
-  flux_tangent(q, zero, k, dalpha, dK, dtau, dtauT, c, f0, F1);
+  flux_tangent<R, true>(q, zero, k, dalpha, dK, dtau, dtauT, c, f0, F1);
   // F1 carries w/h; the test gradient t carries 1/h: multiply by h once
   const R h = R(1) / c.inv_h;
   R acc = f0[0] * t.u[0] + f0[1] * t.u[1] + f0[2] * t.u[2] + f0[3] * t.p + f0[4] * t.T;
@@ -644,6 +673,7 @@ NC_HD ElemCoef<R> lin_coef(const R* cache, long long stride, R gam, R s, const E
   k.tau = cache[(long long)(8 * LIN_GP) * stride];
   k.tauT = cache[(long long)(8 * LIN_GP + 1) * stride];
   k.s = s;
+  scale_coef(k, c);
   return k;
 }
 
@@ -656,8 +686,10 @@ NC_HD void pair_jvp_lin(const R* cache, long long stride, const R ve[5][8], cons
   const R cy = R(gw(P & 1)), cz = R(gw(P >> 1));
   interp_all_pair<R>(ve, c.inv_h, cy, cz, d);
   R f0[2][5], F1[2][5][3];
-  flux_tangent_rm(q[0], rM[0], rT[0], d[0], k, R(0), R(0), dtau, dtauT, c, f0[0], F1[0]);
-  flux_tangent_rm(q[1], rM[1], rT[1], d[1], k, R(0), R(0), dtau, dtauT, c, f0[1], F1[1]);
+  flux_tangent_rm<R, false>(q[0], rM[0], rT[0], d[0], k, R(0), R(0), dtau, dtauT, c, f0[0],
+                            F1[0]);
+  flux_tangent_rm<R, false>(q[1], rM[1], rT[1], d[1], k, R(0), R(0), dtau, dtauT, c, f0[1],
+                            F1[1]);
   test_all_pair<R>(out, cy, cz, f0, F1);
 }
 
@@ -706,7 +738,7 @@ NC_HD void elem_jtvp_lin(const R* cache, long long stride, const R ue[3][8], con
   pair_jtvp_lin<R, 1>(cache, stride, we, k, c, out, tb, tbT);
   pair_jtvp_lin<R, 2>(cache, stride, we, k, c, out, tb, tbT);
   pair_jtvp_lin<R, 3>(cache, stride, we, k, c, out, tb, tbT);
-  const R gsum = -(k.tau * k.tau * k.tau * tb + k.tauT * k.tauT * k.tauT * tbT) * c.inv16h2;
+  const R gsum = -(k.tau * k.tau * k.tau * tb + k.tauT * k.tauT * k.tauT * tbT) * (c.wq * c.inv16h2);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -781,11 +813,17 @@ NC_HD ElemConst<R> make_const(double h, double Gr, double Pr, double amax, doubl
   ElemConst<R> c;
   c.inv_h = R(1.0 / h);
   c.wq = R((h / 2) * (h / 2) * (h / 2));
+  c.wh = R((h / 2) * (h / 2) * (h / 2) / h);
   c.Pr = R(Pr);
   c.beta = R(Gr * Pr * Pr);
   c.eg[0] = R(eg[0]);
   c.eg[1] = R(eg[1]);
   c.eg[2] = R(eg[2]);
+  c.beg[0] = R(Gr * Pr * Pr * eg[0]);
+  c.beg[1] = R(Gr * Pr * Pr * eg[1]);
+  c.beg[2] = R(Gr * Pr * Pr * eg[2]);
+  c.prw = R(Pr * (h / 2) * (h / 2) * (h / 2) / h);
+  c.prw2 = R(2.0 * Pr * (h / 2) * (h / 2) * (h / 2) / h);
   c.inv16h2 = R(1.0 / (16.0 * h * h));
   c.t2inv2 = R((4.0 * Pr / (h * h)) * (4.0 * Pr / (h * h)));
   c.k2c = R((4.0 / (h * h)) * (4.0 / (h * h)));
