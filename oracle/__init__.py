@@ -13,7 +13,11 @@ natural convection" (Alexandersen, Sigmund, Aage):
 * ``element``   element residual of the stabilised weak form (Sec. 2, Sec. 4, App. B)
 * ``assemble``  global residual, complex-step element Jacobians assembled to CSR
 * ``solve``     damped Newton with the polynomial line search (Sec. 5.1), direct
-                linear solves, objective, adjoint and design sensitivities (Sec. 3.2)
+                linear solves, objective, adjoint and design sensitivities (Sec. 3.2),
+                the Gram-Schmidt step of the FGMRES Arnoldi process (Sec. 5.2)
+* ``filter``    the PDE density filter (Sec. 3.2)
+* ``mma``       the method of moving asymptotes for the volume-constrained
+                problem of Sec. 3.2 (one constraint, dual solved by bisection)
 
 Everything is NumPy/SciPy in float64 (complex128 for the complex-step
 derivatives). Nothing is blocked, fused or reordered beyond the definitions.

@@ -507,3 +507,87 @@ def test_gram_schmidt_step_against_least_squares():
         assert abs(np.linalg.norm(q) - 1.0) <= 1e-14
         assert np.max(np.abs(V @ q)) <= 1e-14
         assert np.linalg.norm(V.T @ h + nu * q - w) <= 1e-13 * np.linalg.norm(w)
+
+
+def _mma_instance(rng, n):
+    x = rng.uniform(0.2, 0.8, n)
+    xold1 = np.clip(x + rng.normal(0, 0.05, n), 0, 1)
+    xold2 = np.clip(xold1 + rng.normal(0, 0.05, n), 0, 1)
+    low, upp = x - 0.3, x + 0.3
+    df0 = rng.normal(0, 1, n)
+    df1 = -np.ones(n) / n           # a volume-type constraint: sum (1 - x) / n - vf
+    f1 = 0.05                       # violated by 0.05, reachable within the move limits
+    return x, xold1, xold2, low, upp, f1, df0, df1
+
+
+def test_mma_subproblem_kkt_and_scipy():
+    """MMA (the optimiser of Sec. 3.2): the oracle's step solves its convex
+    subproblem.  KKT: each coordinate strictly inside its move limits is
+    stationary for the Lagrangian, the constraint is active (its multiplier is
+    positive), and on a 6-variable instance the minimiser equals SciPy's SLSQP
+    solution of the same subproblem."""
+    from scipy.optimize import minimize
+    from oracle import mma as M
+    rng = np.random.default_rng(3)
+    for n, k in ((6, 0), (6, 3), (400, 5)):
+        x, xo1, xo2, low, upp, f1, df0, df1 = _mma_instance(rng, n)
+        y, L, U, lam = M.mma_step(k, x, xo1, xo2, low, upp, f1, df0, df1, move=0.2)
+        al, be = M.bounds(x, L, U, 0.0, 1.0, 0.2)
+        p0, q0 = M.approx_coefficients(x, L, U, df0, 1.0)
+        p1, q1 = M.approx_coefficients(x, L, U, df1, 1.0)
+        assert lam > 0
+        assert abs(M.approx_value(f1, x, y, L, U, p1, q1)) <= 1e-12
+        grad = (p0 + lam * p1) / (U - y) ** 2 - (q0 + lam * q1) / (y - L) ** 2
+        inner = (y > al + 1e-9) & (y < be - 1e-9)
+        assert np.all(np.abs(grad[inner]) <= 1e-8 * (1 + np.abs(p0 / (U - y) ** 2)[inner]))
+        assert np.all(grad[y <= al + 1e-9] >= -1e-8) and np.all(grad[y >= be - 1e-9] <= 1e-8)
+        if n == 6:
+            f0t = lambda z: np.sum(p0 / (U - z) + q0 / (z - L))
+            con = {"type": "ineq", "fun": lambda z: -M.approx_value(f1, x, z, L, U, p1, q1)}
+            r = minimize(f0t, x.copy(), bounds=list(zip(al, be)), constraints=[con],
+                         method="SLSQP", options={"ftol": 1e-14, "maxiter": 500})
+            assert np.max(np.abs(r.x - y)) <= 1e-6
+
+
+def test_mma_converges_on_a_convex_problem():
+    """MMA iterations on  min sum c_j / x_j  s.t.  sum x_j <= V, 0.01 <= x <= 1,
+    whose optimum is x_j = V sqrt(c_j) / sum sqrt(c) (Lagrange conditions; all
+    inside the bounds for these c): the objective reaches the optimum to 1e-9
+    and the constraint holds."""
+    from oracle import mma as M
+    rng = np.random.default_rng(4)
+    n, V = 50, 20.0
+    c = rng.uniform(0.5, 2.0, n)
+    xs = V * np.sqrt(c) / np.sum(np.sqrt(c))
+    assert np.all((xs > 0.01) & (xs < 1.0))
+    x = np.full(n, 0.5)
+    xo1 = xo2 = x.copy()
+    low, upp = x - 0.5, x + 0.5
+    for k in range(80):
+        f1 = (np.sum(x) - V) / V
+        y, low, upp, lam = M.mma_step(k, x, xo1, xo2, low, upp, f1, -c / x ** 2,
+                                      np.ones(n) / V, xmin=0.01, xmax=1.0, move=0.2)
+        xo2, xo1, x = xo1, x, y
+    assert np.sum(c / x) <= np.sum(c / xs) * (1 + 1e-9)
+    assert np.sum(x) <= V * (1 + 1e-12)
+
+
+def test_mma_approximation_is_first_order_exact():
+    """The MMA approximation (Svanberg 1987) agrees with the function and its
+    gradient at the expansion point: f~(x) = f(x) and d f~/dy (x) = df/dx for
+    gradients of either sign (central differences of f~, step 1e-6)."""
+    from oracle import mma as M
+    rng = np.random.default_rng(5)
+    n = 30
+    x = rng.uniform(0.2, 0.8, n)
+    low, upp = x - rng.uniform(0.1, 0.5, n), x + rng.uniform(0.1, 0.5, n)
+    df = rng.normal(0, 1, n)
+    p, q = M.approx_coefficients(x, low, upp, df, 1.0)
+    assert M.approx_value(1.7, x, x, low, upp, p, q) == pytest.approx(1.7, abs=1e-15)
+    e = 1e-6
+    for j in range(n):
+        yp, ym = x.copy(), x.copy()
+        yp[j] += e
+        ym[j] -= e
+        fd = (M.approx_value(0.0, x, yp, low, upp, p, q) - M.approx_value(0.0, x, ym, low, upp, p, q)) / (2 * e)
+        assert fd == pytest.approx(df[j], rel=1e-6, abs=1e-8)
