@@ -263,6 +263,60 @@ nc_status nc_newton_solve(nc_ctx* ctx, const double* gamma, double* x_inout,
 nc_status nc_arnoldi_orth(nc_ctx* ctx, long long n, int k, const void* V, long long ldv,
                           void* w, double* h_host, int prec, void* stream);
 
+/* ---- design update (Sec. 3.2: minimise f subject to the volume constraint
+ * g(gamma) = int_{Omega_d} (1 - gamma) dV <= v_f |Omega_d|, 0 <= gamma <= 1, by the
+ * method of moving asymptotes [Svanberg 1987]).  Variables are element values
+ * [n]; `active` (DEVICE, n bytes, may be NULL = all active) marks the design
+ * variables: inactive ones take no part in the constraint and are never
+ * changed by the update. */
+
+/* Normalised volume constraint of a design gamma [n] (DEVICE, double):
+ *   g = sum_active (1 - gamma_e) / (vf * n_active) - 1  (<= 0 when satisfied),
+ * written to *g_host; dgdgamma (DEVICE [n], may be NULL) receives its gradient,
+ * -1/(vf n_active) on active entries and 0 elsewhere (uniform elements, so the
+ * integral is the element sum times h^3).  Synchronous.  NC_ERR_ARG for n < 1,
+ * vf <= 0 or no active variable. */
+nc_status nc_volume(nc_ctx* ctx, long long n, const double* gamma, const unsigned char* active,
+                    double vf, double* g_host, double* dgdgamma, void* stream);
+
+/* MMA options: move limit as a fraction of xmax - xmin, the box bounds, and a
+ * positive factor applied to the objective gradient df0 (its scaling). */
+typedef struct {
+  double move;
+  double xmin, xmax;
+  double df0_scale;
+} nc_mma_opts;
+
+/* Fill opts with defaults (move 0.2, xmin 0, xmax 1, df0_scale 1). */
+void nc_default_mma_opts(nc_mma_opts* opts);
+
+/* out = min(max(in, lo), hi) on active entries and fixed (or 0 when fixed is
+ * NULL) on the others: the physical design from the filtered variables with the
+ * passive elements reset, or a gradient restricted to the design variables
+ * (lo = -inf, hi = +inf, fixed NULL).  All DEVICE [n] double; out may alias in. */
+nc_status nc_design_map(nc_ctx* ctx, long long n, const double* in, const unsigned char* active,
+                        const double* fixed, double lo, double hi, double* out, void* stream);
+
+/* One MMA iteration (iteration number iter, 0-based) for the objective with
+ * gradient df0 (times opts->df0_scale) and one constraint of value f1 (<= 0
+ * when satisfied) with gradient df1 (DEVICE [n] double each).  On entry x is the
+ * current iterate, xold1 / xold2 the two before it and low / upp the previous
+ * asymptotes (the three are ignored for iter < 2); on return x holds the new
+ * iterate, xold1 / xold2 the shifted history and low / upp the asymptotes used
+ * (all DEVICE [n] double, updated in place).  Asymptotes start at
+ * x -/+ 0.5 (xmax - xmin) and then widen by 1.2 / narrow by 0.7 where a variable
+ * moves monotonically / oscillates; move limits 0.1 of the way to the
+ * asymptotes and `move` of the box; Svanberg's convex approximation of both
+ * functions; the subproblem is solved through its dual, bisection on the
+ * multiplier to floating-point resolution (the multiplier goes to
+ * *lambda_host, and max_j |x_new - x| to *change_host; either may be NULL).
+ * Synchronous.  NC_ERR_ARG for invalid sizes or options, NC_ERR_NAN for a
+ * non-finite value. */
+nc_status nc_mma_update(nc_ctx* ctx, long long n, int iter, double* x, double* xold1,
+                        double* xold2, double* low, double* upp, const double* df0, double f1,
+                        const double* df1, const unsigned char* active, const nc_mma_opts* opts,
+                        double* lambda_host, double* change_host, void* stream);
+
 /* Adjoint solve J(x, gamma)^T lambda = rhs (Sec. 3.2) by FGMRES + multigrid on the
  * transposed operators, inside FP64 iterative refinement until
  * ||rhs - J^T lambda|| <= rtol_newton ||rhs||.  All FP64 [5][Nn].  Synchronous. */

@@ -67,6 +67,11 @@ class SolveInfo(ctypes.Structure):
                     res_hist=list(self.res_hist[:k]))
 
 
+class MmaOpts(ctypes.Structure):
+    _fields_ = [("move", ctypes.c_double), ("xmin", ctypes.c_double), ("xmax", ctypes.c_double),
+                ("df0_scale", ctypes.c_double)]
+
+
 _vp = ctypes.c_void_p
 _ctx = ctypes.c_void_p
 _SIGS = {
@@ -97,6 +102,15 @@ _SIGS = {
     "nc_arnoldi_orth": (ctypes.c_int, [_ctx, ctypes.c_longlong, ctypes.c_int, _vp,
                                        ctypes.c_longlong, _vp, ctypes.POINTER(ctypes.c_double),
                                        ctypes.c_int, _vp]),
+    "nc_volume": (ctypes.c_int, [_ctx, ctypes.c_longlong, _vp, _vp, ctypes.c_double,
+                                 ctypes.POINTER(ctypes.c_double), _vp, _vp]),
+    "nc_default_mma_opts": (None, [ctypes.POINTER(MmaOpts)]),
+    "nc_design_map": (ctypes.c_int, [_ctx, ctypes.c_longlong, _vp, _vp, _vp, ctypes.c_double,
+                                     ctypes.c_double, _vp, _vp]),
+    "nc_mma_update": (ctypes.c_int, [_ctx, ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp, _vp,
+                                     _vp, _vp, ctypes.c_double, _vp, _vp,
+                                     ctypes.POINTER(MmaOpts), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double), _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -263,6 +277,58 @@ class Problem:
                                       ctypes.c_void_p(w.data_ptr()), h, self._prec(w),
                                       _stream(stream)))
         return list(h)
+
+    # ---- design update (Sec. 3.2) ------------------------------------------
+    def volume(self, gam, active=None, vf=0.05, grad=None, stream=None):
+        """Normalised volume constraint g = sum_active (1 - gamma)/(vf n_active) - 1
+        (Sec. 3.2) and, into grad if given, its gradient."""
+        n = gam.numel()
+        self._vec(gam, torch.float64, n, "gamma")
+        if active is not None:
+            self._vec(active, torch.uint8, n, "active")
+        if grad is not None:
+            self._vec(grad, torch.float64, n, "grad")
+        g = ctypes.c_double()
+        p = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+        self._chk(lib.nc_volume(self.ctx, n, p(gam), p(active), vf, ctypes.byref(g), p(grad),
+                                _stream(stream)))
+        return g.value
+
+    def design_map(self, v, active=None, fixed=None, lo=-float("inf"), hi=float("inf"), out=None,
+                   stream=None):
+        """clamp(v, lo, hi) on active entries, fixed (or 0) elsewhere."""
+        n = v.numel()
+        out = torch.empty_like(v) if out is None else out
+        self._vec(v, torch.float64, n, "v")
+        self._vec(out, torch.float64, n, "out")
+        if active is not None:
+            self._vec(active, torch.uint8, n, "active")
+        if fixed is not None:
+            self._vec(fixed, torch.float64, n, "fixed")
+        p = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+        self._chk(lib.nc_design_map(self.ctx, n, p(v), p(active), p(fixed), lo, hi, p(out),
+                                    _stream(stream)))
+        return out
+
+    def mma_update(self, it, x, xold1, xold2, low, upp, df0, f1, df1, active=None,
+                   move=0.2, xmin=0.0, xmax=1.0, df0_scale=1.0, stream=None):
+        """One MMA iteration (Sec. 3.2, Svanberg 1987); x, xold1, xold2, low, upp
+        are updated in place.  Returns (constraint multiplier, max |x_new - x|)."""
+        n = x.numel()
+        for t, nm in ((x, "x"), (xold1, "xold1"), (xold2, "xold2"), (low, "low"), (upp, "upp"),
+                      (df0, "df0"), (df1, "df1")):
+            self._vec(t, torch.float64, n, nm)
+        if active is not None:
+            self._vec(active, torch.uint8, n, "active")
+        o = MmaOpts()
+        lib.nc_default_mma_opts(ctypes.byref(o))
+        o.move, o.xmin, o.xmax, o.df0_scale = move, xmin, xmax, df0_scale
+        lam, chg = ctypes.c_double(), ctypes.c_double()
+        p = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+        self._chk(lib.nc_mma_update(self.ctx, n, it, p(x), p(xold1), p(xold2), p(low), p(upp),
+                                    p(df0), float(f1), p(df1), p(active), ctypes.byref(o),
+                                    ctypes.byref(lam), ctypes.byref(chg), _stream(stream)))
+        return lam.value, chg.value
 
     def linearize(self, x, gam, stream=None):
         """Store the linearisation at (x, gamma) (FP64); x and gamma must stay

@@ -1,0 +1,161 @@
+"""Topology optimisation loop of the paper (Sec. 3.2-3.3), driven through the C ABI.
+
+    python -m paper_1508_04596_gb300.optimize WORKLOAD [--iters N] [--steps S]
+                                                       [--nx NX --ny NY --nz NZ] [--fp64]
+
+Per design iteration: the PDE density filter of the design variables, the
+passive elements reset (solid heat-source block, fluid outside the design
+domain), the Newton state solve warm-started from the previous iterate's state
+(load ramping on failure, Sec. 5.1), the objective (thermal compliance with a
+heat source, else the mean patch temperature), the adjoint solve and the
+element sensitivities, the filter's chain rule, the volume constraint and one
+MMA update (Sec. 3.2).  The material parameters follow the paper's five-step
+continuation (Sec. 3.3):
+
+    q_f     0.881, 8.81, 88.1, 881, 881
+    q_alpha 8, 8, 8, 98, 998
+    alpha   1e5, 1e5, 1e5, 1e6, 1e7
+
+with the iterations split evenly over the steps (the paper runs 500 or 1000
+iterations in total and does not give the split).  Every numerical step runs
+in libnc's kernels; this module only orders the calls.
+"""
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import nc, synth
+
+CONTINUATION = [dict(q_f=0.881, q_alpha=8.0, alpha_max=1e5),
+                dict(q_f=8.81, q_alpha=8.0, alpha_max=1e5),
+                dict(q_f=88.1, q_alpha=8.0, alpha_max=1e5),
+                dict(q_f=881.0, q_alpha=98.0, alpha_max=1e6),
+                dict(q_f=881.0, q_alpha=998.0, alpha_max=1e7)]
+
+
+def regions(cfg):
+    """(active design elements, fixed values of the passive elements)."""
+    nx, ny, nz, h = cfg["nx"], cfg["ny"], cfg["nz"], cfg["h"]
+    if cfg.get("bcs") == "quarter":
+        src, des = synth.quarter_regions(nx, ny, nz, h)
+    else:
+        src, des = np.zeros(nx * ny * nz, bool), synth.design_column(nx, ny, nz, h)
+    fixed = np.ones(nx * ny * nz)
+    fixed[src] = 0.0
+    return des, fixed
+
+
+class Optimizer:
+    """State of one optimisation run on a workload (names of synth.WORKLOADS,
+    with optional size overrides nx, ny, nz, h)."""
+
+    def __init__(self, workload, vf=0.05, move=0.2, mixed=1, state_rtol=1e-4, adjoint_rtol=1e-6,
+                 **over):
+        cfg = dict(synth.WORKLOADS[workload])
+        cfg.update(over)
+        self.workload, self.over, self.cfg = workload, over, cfg
+        self.vf, self.move, self.mixed = vf, move, mixed
+        self.state_rtol, self.adjoint_rtol = state_rtol, adjoint_rtol
+        des, fixed = regions(cfg)
+        dev = "cuda"
+        self.active = torch.tensor(des.astype(np.uint8), device=dev)
+        self.fixed = torch.tensor(fixed, dtype=torch.float64, device=dev)
+        rho0 = np.where(des, 1.0 - vf, fixed)  # the uniform start at the volume fraction
+        self.rho = torch.tensor(rho0, dtype=torch.float64, device=dev)
+        self.xold1 = torch.tensor(rho0, dtype=torch.float64, device=dev)
+        self.xold2 = torch.tensor(rho0, dtype=torch.float64, device=dev)
+        E = self.rho.numel()
+        self.low = torch.zeros(E, dtype=torch.float64, device=dev)
+        self.upp = torch.ones(E, dtype=torch.float64, device=dev)
+        self.k = 0
+        self.prob = None
+        self.step = -1
+        self.x = None
+        self.f0_scale = None
+
+    def set_step(self, step):
+        """Material parameters of continuation step `step` (a new context; the
+        state and the MMA history carry over)."""
+        if step == self.step:
+            return
+        kw = dict(self.over)
+        kw.update(CONTINUATION[step])
+        if self.cfg.get("bcs") != "quarter":
+            kw["patch"] = "flux"
+        self.prob = nc.Problem.from_workload(self.workload, **kw)
+        if self.x is None:
+            self.x = torch.zeros(self.prob.ndof, dtype=torch.float64, device="cuda")
+        self.step = step
+
+    def physical(self):
+        """Filtered design, clamped to [0, 1], passive elements reset."""
+        g = self.prob.filter(self.rho)
+        return self.prob.design_map(g, self.active, self.fixed, 0.0, 1.0, out=g)
+
+    def iterate(self):
+        """One design iteration; returns its report."""
+        p = self.prob
+        t0 = time.perf_counter()
+        gam = self.physical()
+        sopts = nc.default_opts(mixed=self.mixed, rtol_newton=self.state_rtol, ramp_steps=3)
+        _, sinf = p.newton_solve(gam, self.x, sopts, check=False)
+        phi, dphi = p.objective(self.x)
+        aopts = nc.default_opts(mixed=self.mixed, rtol_newton=self.adjoint_rtol)
+        lam, ainf = p.adjoint_solve(self.x, gam, -dphi, opts=aopts, check=False)
+        sens = p.sensitivity(self.x, gam, lam)
+        # chain rule of the filter (symmetric) on the design variables only
+        dfdrho = p.filter(p.design_map(sens, self.active, out=sens))
+        dg = torch.empty_like(gam)
+        g = p.volume(gam, self.active, self.vf, grad=dg)
+        dgdrho = p.filter(dg)
+        if self.f0_scale is None:
+            self.f0_scale = 1.0 / max(abs(phi), 1e-300)
+        lam_v, change = p.mma_update(self.k, self.rho, self.xold1, self.xold2, self.low,
+                                     self.upp, dfdrho, g, dgdrho, active=self.active,
+                                     move=self.move, df0_scale=self.f0_scale)
+        self.k += 1
+        torch.cuda.synchronize()
+        return {"iter": self.k, "step": self.step, "phi": phi, "g": g, "change": change,
+                "multiplier": lam_v, "newton_its": sinf["newton_its"],
+                "lin_its": sinf["lin_its_total"], "state_status": sinf["status"],
+                "adjoint_lin_its": ainf["lin_its_total"], "adjoint_status": ainf["status"],
+                "s": round(time.perf_counter() - t0, 4)}
+
+
+def run(workload, iters, steps=5, log=print, **kw):
+    """`iters` design iterations over the first `steps` continuation steps."""
+    opt = Optimizer(workload, **kw)
+    per = max(1, iters // steps)
+    hist = []
+    for it in range(iters):
+        opt.set_step(min(it // per, steps - 1, len(CONTINUATION) - 1))
+        r = opt.iterate()
+        hist.append(r)
+        if log:
+            log(json.dumps(r))
+    return opt, hist
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("workload")
+    ap.add_argument("--iters", type=int, default=25)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--nx", type=int)
+    ap.add_argument("--ny", type=int)
+    ap.add_argument("--nz", type=int)
+    ap.add_argument("--fp64", action="store_true")
+    a = ap.parse_args(argv)
+    over = {}
+    if a.nx:
+        cfg = synth.WORKLOADS[a.workload]
+        over = dict(nx=a.nx, ny=a.ny or a.nx, nz=a.nz or a.nx)
+        over["h"] = cfg["h"] * cfg["nz"] / over["nz"]
+    run(a.workload, a.iters, a.steps, mixed=0 if a.fp64 else 1, **over)
+
+
+if __name__ == "__main__":
+    main()

@@ -339,3 +339,74 @@ def test_arnoldi_orth_matches_oracle(nc, n, k, ldv):
             ho, nuo, qo = S.gram_schmidt_twice(Vr, w0r)
             assert rel(h[:k], ho) <= tol and abs(h[k] - nuo) <= tol * nuo, (dt, rep)
             assert rel(host(w), qo) <= tol, (dt, rep)
+
+
+def _mma_case(rng, n):
+    x = rng.uniform(0.05, 0.95, n)
+    xo1 = np.clip(x + rng.normal(0, 0.05, n), 0, 1)
+    xo2 = np.clip(xo1 + rng.normal(0, 0.05, n), 0, 1)
+    low, upp = x - rng.uniform(0.05, 0.6, n), x + rng.uniform(0.05, 0.6, n)
+    df0 = rng.normal(0, 1, n) * rng.uniform(0, 3, n)
+    df1 = -rng.uniform(0.5, 1.5, n) / n
+    return x, xo1, xo2, low, upp, df0, df1
+
+
+@pytest.mark.parametrize("n,k,f1", [(10007, 0, 0.03), (10007, 1, 0.03), (10007, 4, 0.03),
+                                    (10007, 4, -0.5), (257, 7, 0.01)])
+def test_mma_update_matches_oracle(nc, n, k, f1):
+    """One MMA iteration (Sec. 3.2, Svanberg 1987) through nc_mma_update against
+    the oracle's step on the active variables (a seeded mask of about 60 %):
+    new iterate, asymptotes and multiplier to 1e-10; inactive variables keep
+    their value; the history shifts; the reported change is max |x_new - x|.
+    Cases: the first two iterations (fixed asymptotes), later iterations
+    (adapted asymptotes), an inactive constraint (multiplier 0) and a small
+    ragged size.  The objective gradient goes in divided by 4 with
+    df0_scale = 4."""
+    from oracle import mma as M
+    rng = np.random.default_rng(n + k)
+    x, xo1, xo2, low, upp, df0, df1 = _mma_case(rng, n)
+    a = rng.uniform(0, 1, n) < 0.6
+    yo, Lo, Uo, lo = M.mma_step(k, x[a], xo1[a], xo2[a], low[a], upp[a], f1, df0[a], df1[a],
+                                move=0.2)
+    gp = nc.Problem(nc.make_params(2, 2, 2, 0.5, 1e3, 0.71), nc.cavity_bcs())
+    X, X1, X2, L, U = dev(x), dev(xo1), dev(xo2), dev(low), dev(upp)
+    lam, chg = gp.mma_update(k, X, X1, X2, L, U, dev(df0 / 4.0), f1, dev(df1),
+                             active=torch.tensor(a.astype(np.uint8), device="cuda"),
+                             df0_scale=4.0)
+    assert lam == pytest.approx(lo, rel=1e-10, abs=1e-300)
+    assert np.max(np.abs(host(X)[a] - yo)) <= 1e-10
+    assert np.array_equal(host(X)[~a], x[~a])
+    assert np.array_equal(host(X1), x) and np.array_equal(host(X2), xo1)
+    assert np.max(np.abs(host(L)[a] - Lo)) <= 1e-12 and np.max(np.abs(host(U)[a] - Uo)) <= 1e-12
+    assert chg == pytest.approx(np.max(np.abs(host(X) - x)), rel=1e-12)
+
+
+def test_volume_matches_numpy(nc):
+    """Normalised volume constraint (Sec. 3.2) and its gradient against numpy,
+    with and without a design mask; a ragged size."""
+    rng = np.random.default_rng(21)
+    n = 33333
+    g = rng.uniform(0, 1, n)
+    act = rng.uniform(0, 1, n) < 0.3
+    gp = nc.Problem(nc.make_params(2, 2, 2, 0.5, 1e3, 0.71), nc.cavity_bcs())
+    grad = torch.empty(n, dtype=torch.float64, device="cuda")
+    v = gp.volume(dev(g), torch.tensor(act.astype(np.uint8), device="cuda"), vf=0.05, grad=grad)
+    assert v == pytest.approx(np.sum(1 - g[act]) / (0.05 * act.sum()) - 1, rel=1e-13)
+    assert np.allclose(host(grad), np.where(act, -1 / (0.05 * act.sum()), 0.0), rtol=1e-15, atol=0)
+    assert gp.volume(dev(g), None, vf=0.5) == pytest.approx(np.sum(1 - g) / (0.5 * n) - 1, rel=1e-13)
+
+
+def test_design_map(nc):
+    """Physical design from filtered variables: clamp on the design variables,
+    fixed values elsewhere; a gradient restricted to the design variables."""
+    rng = np.random.default_rng(22)
+    n = 1001
+    v = rng.normal(0.5, 0.6, n)
+    act = rng.uniform(0, 1, n) < 0.5
+    fixed = rng.uniform(0, 1, n)
+    gp = nc.Problem(nc.make_params(2, 2, 2, 0.5, 1e3, 0.71), nc.cavity_bcs())
+    a = torch.tensor(act.astype(np.uint8), device="cuda")
+    out = gp.design_map(dev(v), a, dev(fixed), 0.0, 1.0)
+    assert np.array_equal(host(out), np.where(act, np.clip(v, 0, 1), fixed))
+    out = gp.design_map(dev(v), a)
+    assert np.array_equal(host(out), np.where(act, v, 0.0))

@@ -189,3 +189,19 @@ def test_newton_ramping_recovers(nc):
     r = prob.residual(x, gam).norm().item()
     assert r <= 1e-8 * r0
     assert info["res0"] == pytest.approx(r0, rel=1e-12)
+
+
+def test_optimisation_loop_quarter_cavity(nc):
+    """The optimisation loop of Sec. 3.2-3.3 on the paper's quarter cavity at
+    16 x 16 x 32 (Gr = 1e3, first continuation step): filter, Newton state
+    solve, thermal compliance, adjoint, sensitivities, volume constraint and MMA
+    for 10 iterations from the uniform design at the volume fraction.  Every
+    solve converges, the thermal compliance decreases, the volume constraint
+    holds at the end (g <= 1e-3) and no variable moves more than the move limit."""
+    from paper_1508_04596_gb300 import optimize
+    opt, hist = optimize.run("quarter80x80x160_gr1e3", 10, steps=1, log=None,
+                             nx=16, ny=16, nz=32, h=1.0 / 32)
+    assert all(r["state_status"] == "NC_OK" and r["adjoint_status"] == "NC_OK" for r in hist), hist
+    assert hist[-1]["phi"] < hist[0]["phi"], [r["phi"] for r in hist]
+    assert hist[-1]["g"] <= 1e-3, [r["g"] for r in hist]
+    assert all(0.0 <= r["change"] <= 0.2 + 1e-12 for r in hist)
