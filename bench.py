@@ -279,7 +279,7 @@ def run_ours(args, rank, world):
     peak = ALU_PEAK_TFLOPS[args.prec]
     # DRAM bytes (read + write) of one element-kernel launch from the 128^3 ncu captures
     # of this kernel version (profiles/k_elem_lin_cavity128.md), scaled by elements
-    traffic = {"f64": 2750.17e6 + 1033.92e6, "f32": 96.55e6 + 278.28e6}[args.prec] \
+    traffic = {"f64": 2743.35e6 + 949.11e6, "f32": 96.49e6 + 278.01e6}[args.prec] \
         * prob.E / 2097152
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
             "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
