@@ -223,6 +223,10 @@ typedef struct {
   int mixed;
   int ramp_steps;
   double atol_newton;  /* also stop when ||R|| <= atol_newton (default 0) */
+  int galerkin;        /* 1: coarse-level operators are the Galerkin products P^T A P of the
+                          level above (the paper's choice, Sec. 5.2), built by probing once
+                          per linearisation and applied as 27-point block stencils; 0
+                          (default): rediscretised at the injected state and averaged design */
 } nc_solve_opts;
 
 /* Per-solve report (Sec. 6.2 reports Newton and linear iteration counts). */
@@ -234,7 +238,7 @@ typedef struct {
 
 /* Fill opts with defaults (rtol_newton 1e-8, rtol_lin 1e-5, max_newton 30,
  * max_lin 200, restart 30, all levels, smooth_its 6, coarse_its 30, mixed 1,
- * ramp_steps 0). */
+ * ramp_steps 0, atol_newton 0, galerkin 0). */
 void nc_default_opts(nc_solve_opts* opts);
 
 /* Damped Newton (Sec. 5.1) on R(x, gamma) = 0 from x_inout (Dirichlet values
@@ -316,6 +320,22 @@ nc_status nc_mma_update(nc_ctx* ctx, long long n, int iter, double* x, double* x
                         double* xold2, double* low, double* upp, const double* df0, double f1,
                         const double* df1, const unsigned char* active, const nc_mma_opts* opts,
                         double* lambda_host, double* change_host, void* stream);
+
+/* Grid of multigrid level `level` (0 = the problem's grid; each level halves the
+ * element counts while all of them stay even and at least 2): dims = {nx, ny, nz}. */
+nc_status nc_level_dims(nc_ctx* ctx, int level, int* dims);
+
+/* Apply the operator of multigrid level `level` as the solvers build it at the
+ * linearisation point (x, gamma) (FP64 [5][Nn] and [E] of level 0): out = A_l v,
+ * or A_l^T v with transpose.  Level 0 is the Jacobian J(x, gamma); coarser
+ * levels are rediscretised at the injected state and the averaged design
+ * (galerkin = 0) or the Galerkin products P^T A_{l-1} P of the trilinear
+ * prolongation P (galerkin = 1, Sec. 5.2), with Dirichlet unknowns as identity
+ * rows and removed columns.  v, out: DEVICE [5][Nn_l] of double (NC_FP64) or
+ * float (NC_FP32, the mixed-precision hierarchy).  Builds the hierarchy's
+ * linearisation first (the cost of a solver's linearisation).  Synchronous. */
+nc_status nc_mg_apply(nc_ctx* ctx, int level, const double* x, const double* gamma, const void* v,
+                      void* out, int prec, int transpose, int galerkin, void* stream);
 
 /* Adjoint solve J(x, gamma)^T lambda = rhs (Sec. 3.2) by FGMRES + multigrid on the
  * transposed operators, inside FP64 iterative refinement until

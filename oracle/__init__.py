@@ -18,6 +18,8 @@ natural convection" (Alexandersen, Sigmund, Aage):
 * ``filter``    the PDE density filter (Sec. 3.2)
 * ``mma``       the method of moving asymptotes for the volume-constrained
                 problem of Sec. 3.2 (one constraint, dual solved by bisection)
+* ``multigrid`` the trilinear prolongation and the Galerkin coarse operator
+                P^T A P of the multigrid preconditioner (Sec. 5.2)
 
 Everything is NumPy/SciPy in float64 (complex128 for the complex-step
 derivatives). Nothing is blocked, fused or reordered beyond the definitions.

@@ -119,6 +119,10 @@ void free_level(Level& L) {
   cudaFree(L.f32.lin);
   L.f64.lin = nullptr;
   L.f32.lin = nullptr;
+  cudaFree(L.f64.gst);
+  cudaFree(L.f32.gst);
+  L.f64.gst = nullptr;
+  L.f32.gst = nullptr;
 }
 
 bool check_prec(int prec) { return prec == NC_FP64 || prec == NC_FP32; }

@@ -199,6 +199,49 @@ nc_status coarse_setup(nc_ctx* ctx, Level& L, const R* x, const R* gam, const R*
 }
 
 template <typename R>
+nc_status coarse_setup_stencil(nc_ctx* ctx, Level& L, const R* S, R** inv_dev, cudaStream_t s) {
+  const int n = coarse_dense_dofs(L);
+  const LevelDev& d = L.d;
+  const long long Nn = d.Nn;
+  nc_status st;
+  if (!*inv_dev) {
+    if ((st = cuda_check(ctx, cudaMalloc((void**)inv_dev, sizeof(R) * (size_t)n * n),
+                         "cudaMalloc coarse inverse")) != NC_OK)
+      return st;
+  }
+  std::vector<R> sh((size_t)GALERKIN_STENCIL * Nn);
+  if ((st = cuda_check(ctx, cudaMemcpyAsync(sh.data(), S, sizeof(R) * sh.size(),
+                                            cudaMemcpyDeviceToHost, s), "coarse stencil D2H")) != NC_OK ||
+      (st = cuda_check(ctx, cudaStreamSynchronize(s), "coarse sync")) != NC_OK)
+    return st;
+  // dense assembly, unknown index f * Nn + node; Dirichlet rows are identity rows
+  // of the stencil already
+  std::vector<double> A((size_t)n * n, 0.0);
+  for (long long node = 0; node < Nn; ++node) {
+    const int i = (int)(node % (d.nx + 1));
+    const long long t = node / (d.nx + 1);
+    const int j = (int)(t % (d.ny + 1));
+    const int k = (int)(t / (d.ny + 1));
+    for (int o = 0; o < 27; ++o) {
+      const int ii = i + o % 3 - 1, jj = j + (o / 3) % 3 - 1, kk = k + o / 9 - 1;
+      if (ii < 0 || ii > d.nx || jj < 0 || jj > d.ny || kk < 0 || kk > d.nz) continue;
+      const long long m = ii + (long long)(d.nx + 1) * (jj + (long long)(d.ny + 1) * kk);
+      for (int f = 0; f < 5; ++f)
+        for (int g = 0; g < 5; ++g)
+          A[(size_t)(f * Nn + node) * n + (g * Nn + m)] =
+              (double)sh[(size_t)((o * 5 + f) * 5 + g) * Nn + node];
+    }
+  }
+  if (!gauss_jordan_inverse(A, n))
+    return set_err(ctx, NC_ERR_NAN, "coarsest-level Galerkin operator is singular");
+  std::vector<R> Ar(A.begin(), A.end());
+  if ((st = cuda_check(ctx, cudaMemcpyAsync(*inv_dev, Ar.data(), sizeof(R) * Ar.size(),
+                                            cudaMemcpyHostToDevice, s), "coarse H2D")) != NC_OK)
+    return st;
+  return cuda_check(ctx, cudaStreamSynchronize(s), "coarse sync");
+}
+
+template <typename R>
 void coarse_apply(const Level& L, bool tr, const R* inv, const R* b, R* z, cudaStream_t s) {
   const int n = coarse_dense_dofs(L);
   if (tr)
@@ -213,6 +256,10 @@ template nc_status coarse_setup<float>(nc_ctx*, Level&, const float*, const floa
                                        float**, cudaStream_t);
 template void coarse_apply<double>(const Level&, bool, const double*, const double*, double*,
                                    cudaStream_t);
+template nc_status coarse_setup_stencil<double>(nc_ctx*, Level&, const double*, double**,
+                                                cudaStream_t);
+template nc_status coarse_setup_stencil<float>(nc_ctx*, Level&, const float*, float**,
+                                               cudaStream_t);
 template void coarse_apply<float>(const Level&, bool, const float*, const float*, float*,
                                   cudaStream_t);
 

@@ -52,6 +52,8 @@ struct LevelBuf {
   bool ext = false;    // x and gam point to caller/Newton arrays (level 0, FP64)
   R* inv = nullptr;    // dense inverse of the level operator (coarsest level only)
   R* lin = nullptr;    // linearisation cache (FP64 levels)
+  R* gst = nullptr;    // Galerkin coarse operator, 27-point stencil of 5x5 blocks (levels >= 1)
+  bool use_gst = false;  // the current linearisation uses gst on this level
 };
 
 struct Level {
@@ -206,6 +208,20 @@ template <typename R>
 void vcombine(long long n, int k, const R* X, long long ld, const double* coef, const R* D, R* z,
               bool accumulate, cudaStream_t s);
 
+// ---- Galerkin coarse operators (nc_galerkin.cu): S holds 675 * Nn entries,
+// S[((o*5 + f)*5 + g)*Nn + n] couples (n, f) to (n + offset o, g)
+constexpr int GALERKIN_STENCIL = 675;
+template <typename R>
+void op_stencil(const LevelDev& d, const R* S, bool tr, const R* v, R* out, cudaStream_t s);
+template <typename R>
+void op_stencil_diag(const LevelDev& d, const R* S, R* out, cudaStream_t s);
+template <typename R>
+void galerkin_probe_init(const LevelDev& d, int c, int g, R* v, cudaStream_t s);
+template <typename R>
+void galerkin_probe_scatter(const LevelDev& d, int c, int g, const R* r, R* S, cudaStream_t s);
+template <typename R>
+void galerkin_dirichlet(const LevelDev& d, R* S, cudaStream_t s);
+
 // ---- coarsest-level direct solve (nc_coarse.cu)
 constexpr int COARSE_DENSE_MAX = 1000;  // largest coarsest level solved by a dense inverse
 int coarse_dense_dofs(const Level& L);
@@ -214,5 +230,8 @@ nc_status coarse_setup(nc_ctx* ctx, Level& L, const R* x, const R* gam, const R*
                        cudaStream_t s);
 template <typename R>
 void coarse_apply(const Level& L, bool tr, const R* inv, const R* b, R* z, cudaStream_t s);
+// dense inverse of a level's Galerkin stencil operator
+template <typename R>
+nc_status coarse_setup_stencil(nc_ctx* ctx, Level& L, const R* S, R** inv, cudaStream_t s);
 
 }  // namespace nc

@@ -110,6 +110,10 @@ template <typename R>
 void level_apply(nc_ctx* ctx, int l, bool tr, const R* v, R* out, cudaStream_t s) {
   Level& L = ctx->lv[l];
   LevelBuf<R>& B = buf<R>(L);
+  if (l > 0 && B.use_gst) {  // Galerkin coarse operator
+    op_stencil<R>(L.d, B.gst, tr, v, out, s);
+    return;
+  }
   if (B.lin) {  // FP64 levels: products from the linearisation cache
     if (tr)
       op_jtvp_cached<R>(L.d, cst<R>(L), B.x, B.gam, B.src, B.lin, v, out, (R*)ctx->Y, s);
@@ -204,6 +208,9 @@ nc_status alloc_levels(nc_ctx* ctx, int nlev, const nc_solve_opts& o) {
     if (sizeof(R) == sizeof(double) &&
         (st = alloc(ctx, &B.lin, (long long)LIN_SLOTS * L.d.E)) != NC_OK)
       return st;
+    if (o.galerkin && l >= 1 &&
+        (st = alloc(ctx, &B.gst, (long long)GALERKIN_STENCIL * L.d.Nn)) != NC_OK)
+      return st;
     const bool level0_f64 = (l == 0) && sizeof(R) == sizeof(double);
     if (!level0_f64) {
       if ((st = alloc(ctx, &B.x, n)) != NC_OK || (st = alloc(ctx, &B.gam, L.d.E)) != NC_OK)
@@ -213,11 +220,34 @@ nc_status alloc_levels(nc_ctx* ctx, int nlev, const nc_solve_opts& o) {
   return NC_OK;
 }
 
+// Galerkin operator of level l >= 1 from level l - 1's operator, by probing
+// (27 colours x 5 fields; see nc_galerkin.cu).
+template <typename R>
+void galerkin_build(nc_ctx* ctx, int l, cudaStream_t s) {
+  Level& F = ctx->lv[l - 1];
+  Level& L = ctx->lv[l];
+  LevelBuf<R>& BF = buf<R>(F);
+  LevelBuf<R>& BL = buf<R>(L);
+  const long long nf = 5 * F.d.Nn;
+  for (int c = 0; c < 27; ++c)
+    for (int g = 0; g < 5; ++g) {
+      galerkin_probe_init<R>(L.d, c, g, BL.t, s);
+      vzero(nf, BF.t, s);
+      op_prolong_add<R>(L.d, (const R*)BL.t, F.d, BF.t, s);
+      level_apply<R>(ctx, l - 1, false, (const R*)BF.t, BF.r, s);
+      op_restrict<R>(F.d, (const R*)BF.r, L.d, BL.r, s);
+      galerkin_probe_scatter<R>(L.d, c, g, (const R*)BL.r, BL.gst, s);
+    }
+  galerkin_dirichlet<R>(L.d, BL.gst, s);
+}
+
 // Linearisation data of every level in precision R at (x, gamma) (FP64 inputs):
 // level 0 is x, gamma themselves (FP64) or their FP32 casts; coarser levels take
-// the injected state and the mean design of the eight children; then diag(J).
+// the injected state and the mean design of the eight children and are
+// rediscretised there, or (galerkin) hold P^T A P of the level above; then diag(J).
 template <typename R>
-nc_status linearize(nc_ctx* ctx, int nlev, const double* x, const double* gam, cudaStream_t s) {
+nc_status linearize(nc_ctx* ctx, int nlev, const double* x, const double* gam, cudaStream_t s,
+                    bool galerkin) {
   for (int l = 0; l < nlev; ++l) {
     Level& L = ctx->lv[l];
     LevelBuf<R>& B = buf<R>(L);
@@ -235,11 +265,18 @@ nc_status linearize(nc_ctx* ctx, int nlev, const double* x, const double* gam, c
       op_inject<R>(F.d, buf<R>(F).x, L.d, B.x, s);
       op_coarsen_elem<R>(F.d, buf<R>(F).gam, L.d, B.gam, s);
     }
-    // diag(J^T) = diag(J)
-    op_diag<R>(L.d, cst<R>(L), B.x, B.gam, B.src, B.diag, (R*)ctx->Y, s);
-    if (B.lin) op_linearize<R>(L.d, cst<R>(L), B.x, B.gam, B.src, B.lin, s);
+    B.use_gst = galerkin && l >= 1;
+    if (B.use_gst) {
+      galerkin_build<R>(ctx, l, s);
+      op_stencil_diag<R>(L.d, B.gst, B.diag, s);
+    } else {
+      // diag(J^T) = diag(J)
+      op_diag<R>(L.d, cst<R>(L), B.x, B.gam, B.src, B.diag, (R*)ctx->Y, s);
+      if (B.lin) op_linearize<R>(L.d, cst<R>(L), B.x, B.gam, B.src, B.lin, s);
+    }
     if (l == nlev - 1 && coarse_dense_dofs(L) <= COARSE_DENSE_MAX) {
-      const nc_status st = coarse_setup<R>(ctx, L, B.x, B.gam, B.src, &B.inv, s);
+      const nc_status st = B.use_gst ? coarse_setup_stencil<R>(ctx, L, B.gst, &B.inv, s)
+                                     : coarse_setup<R>(ctx, L, B.x, B.gam, B.src, &B.inv, s);
       if (st != NC_OK) return st;
     } else if (B.inv) {
       cudaFree(B.inv);  // a previous solve used this level as the coarsest
@@ -561,7 +598,8 @@ nc_status newton(nc_ctx* ctx, const double* gam, double* x, const nc_solve_opts&
       info->res_final = nr;
       return set_err(ctx, NC_ERR_MAXIT, "Newton reached max_newton");
     }
-    st = mixed ? linearize<float>(ctx, nlev, x, gam, s) : linearize<double>(ctx, nlev, x, gam, s);
+    st = mixed ? linearize<float>(ctx, nlev, x, gam, s, o.galerkin != 0)
+               : linearize<double>(ctx, nlev, x, gam, s, o.galerkin != 0);
     if (st != NC_OK) return st;
     // J d = R, the Newton step is -d
     int lits = 0;
@@ -627,6 +665,7 @@ void nc_default_opts(nc_solve_opts* o) {
   o->mixed = 1;
   o->ramp_steps = 0;
   o->atol_newton = 0.0;
+  o->galerkin = 0;
 }
 
 nc_status nc_newton_solve(nc_ctx* ctx, const double* gam, double* x, const nc_solve_opts* opts,
@@ -729,6 +768,44 @@ nc_status nc_arnoldi_orth(nc_ctx* ctx, long long n, int k, const void* V, long l
   return NC_OK;
 }
 
+nc_status nc_level_dims(nc_ctx* ctx, int level, int* dims) {
+  if (!ctx) return NC_ERR_ARG;
+  if (!dims || level < 0 || level >= (int)ctx->lv.size())
+    return set_err(ctx, NC_ERR_ARG, "nc_level_dims: invalid level");
+  dims[0] = ctx->lv[level].d.nx;
+  dims[1] = ctx->lv[level].d.ny;
+  dims[2] = ctx->lv[level].d.nz;
+  return NC_OK;
+}
+
+nc_status nc_mg_apply(nc_ctx* ctx, int level, const double* x, const double* gam, const void* v,
+                      void* out, int prec, int transpose, int galerkin, void* stream) {
+  if (!ctx) return NC_ERR_ARG;
+  if (!x || !gam || !v || !out || level < 0 || level >= (int)ctx->lv.size() ||
+      (prec != NC_FP64 && prec != NC_FP32))
+    return set_err(ctx, NC_ERR_ARG, "nc_mg_apply: invalid argument");
+  nc_solve_opts o;
+  nc_default_opts(&o);
+  o.galerkin = galerkin != 0;
+  const int nlev = level + 1;
+  o.mg_levels = nlev;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool mixed = prec == NC_FP32;
+  nc_status st = prepare(ctx, o, nlev, mixed);
+  if (st != NC_OK) return st;
+  st = mixed ? linearize<float>(ctx, nlev, x, gam, s, o.galerkin != 0)
+             : linearize<double>(ctx, nlev, x, gam, s, o.galerkin != 0);
+  if (st == NC_OK) {
+    if (mixed)
+      level_apply<float>(ctx, level, transpose != 0, (const float*)v, (float*)out, s);
+    else
+      level_apply<double>(ctx, level, transpose != 0, (const double*)v, (double*)out, s);
+  }
+  release_ext(ctx);
+  const nc_status st2 = cuda_check(ctx, cudaStreamSynchronize(s), "nc_mg_apply");
+  return st != NC_OK ? st : st2;
+}
+
 nc_status nc_adjoint_solve(nc_ctx* ctx, const double* x, const double* gam, const double* rhs,
                            double* lam, const nc_solve_opts* opts, nc_solve_info* info_out,
                            void* stream) {
@@ -764,7 +841,8 @@ nc_status nc_adjoint_solve(nc_ctx* ctx, const double* x, const double* gam, cons
     while (st == NC_OK && nr > o.rtol_newton * nb && nr > 0.0) {
       if (k >= o.max_newton) { st = set_err(ctx, NC_ERR_MAXIT, "adjoint refinement limit"); break; }
       if (!linearized) {
-        st = mixed ? linearize<float>(ctx, nlev, x, gam, s) : linearize<double>(ctx, nlev, x, gam, s);
+        st = mixed ? linearize<float>(ctx, nlev, x, gam, s, o.galerkin != 0)
+                   : linearize<double>(ctx, nlev, x, gam, s, o.galerkin != 0);
         if (st != NC_OK) break;
         linearized = true;
       }

@@ -50,7 +50,7 @@ class SolveOpts(ctypes.Structure):
                 ("restart", ctypes.c_int), ("mg_levels", ctypes.c_int),
                 ("smooth_its", ctypes.c_int), ("coarse_its", ctypes.c_int),
                 ("mixed", ctypes.c_int), ("ramp_steps", ctypes.c_int),
-                ("atol_newton", ctypes.c_double)]
+                ("atol_newton", ctypes.c_double), ("galerkin", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -102,6 +102,9 @@ _SIGS = {
     "nc_arnoldi_orth": (ctypes.c_int, [_ctx, ctypes.c_longlong, ctypes.c_int, _vp,
                                        ctypes.c_longlong, _vp, ctypes.POINTER(ctypes.c_double),
                                        ctypes.c_int, _vp]),
+    "nc_level_dims": (ctypes.c_int, [_ctx, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "nc_mg_apply": (ctypes.c_int, [_ctx, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_int, _vp]),
     "nc_volume": (ctypes.c_int, [_ctx, ctypes.c_longlong, _vp, _vp, ctypes.c_double,
                                  ctypes.POINTER(ctypes.c_double), _vp, _vp]),
     "nc_default_mma_opts": (None, [ctypes.POINTER(MmaOpts)]),
@@ -277,6 +280,26 @@ class Problem:
                                       ctypes.c_void_p(w.data_ptr()), h, self._prec(w),
                                       _stream(stream)))
         return list(h)
+
+    # ---- multigrid levels (Sec. 5.2) ---------------------------------------
+    def level_dims(self, level):
+        d = (ctypes.c_int * 3)()
+        self._chk(lib.nc_level_dims(self.ctx, level, d))
+        return tuple(d)
+
+    def mg_apply(self, level, x, gam, v, out=None, transpose=False, galerkin=False, stream=None):
+        """out = A_l v (or A_l^T v) with the multigrid level-l operator built at
+        (x, gamma); v and out hold 5 (nx_l+1)(ny_l+1)(nz_l+1) values."""
+        nx, ny, nz = self.level_dims(level)
+        n = 5 * (nx + 1) * (ny + 1) * (nz + 1)
+        out = torch.empty_like(v) if out is None else out
+        self._vec(v, v.dtype, n, "v")
+        self._vec(out, v.dtype, n, "out")
+        self._chk(lib.nc_mg_apply(self.ctx, level, self._vec(x, torch.float64, self.ndof, "x"),
+                                  self._vec(gam, torch.float64, self.E, "gamma"),
+                                  ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                  self._prec(v), int(transpose), int(galerkin), _stream(stream)))
+        return out
 
     # ---- design update (Sec. 3.2) ------------------------------------------
     def volume(self, gam, active=None, vf=0.05, grad=None, stream=None):

@@ -591,3 +591,42 @@ def test_mma_approximation_is_first_order_exact():
         ym[j] -= e
         fd = (M.approx_value(0.0, x, yp, low, upp, p, q) - M.approx_value(0.0, x, ym, low, upp, p, q)) / (2 * e)
         assert fd == pytest.approx(df[j], rel=1e-6, abs=1e-8)
+
+
+def test_prolongation_reproduces_trilinear_fields():
+    """The multigrid prolongation (Sec. 5.2) is trilinear interpolation: a field
+    a + b x + c y + d z + e xyz given at the coarse nodes is reproduced exactly
+    at the fine nodes (away from Dirichlet unknowns, none here)."""
+    from oracle import multigrid as MG
+    gf = G.Grid(4, 6, 2, 0.25)
+    gc = MG.coarse_grid(gf)
+    none_f, none_c = np.zeros((5, gf.Nn), bool), np.zeros((5, gc.Nn), bool)
+    P = MG.prolongation(gf, gc, none_f, none_c)
+    f = lambda p: 1.0 + 2 * p[:, 0] - 3 * p[:, 1] + 0.5 * p[:, 2] + 4 * p[:, 0] * p[:, 1] * p[:, 2]
+    xc = np.tile(f(gc.node_xyz()), 5)
+    assert np.allclose(P @ xc, np.tile(f(gf.node_xyz()), 5), rtol=0, atol=1e-13)
+
+
+def test_galerkin_conduction_block_is_the_coarse_operator():
+    """Variational property of nested Q1 spaces: at rest (u = 0) and uniform
+    design, the temperature block of the Jacobian is the conduction stiffness
+    K int grad N . grad N (no stabilisation acts at u = 0), and its Galerkin
+    projection P^T J_f P equals the coarse grid's own conduction block exactly
+    (the trilinear prolongation is the exact embedding of the coarse space)."""
+    from oracle import multigrid as MG
+    from tests.helpers import oracle_problem
+    nf = 4
+    pf, _ = oracle_problem(nf, nf, nf, 1.0 / nf, 0.0, 0.71)
+    pc, _ = oracle_problem(nf // 2, nf // 2, nf // 2, 2.0 / nf, 0.0, 0.71)
+    gam_f, gam_c = np.full(pf.g.E, 0.4), np.full(pc.g.E, 0.4)
+    xf, xc = np.zeros((5, pf.g.Nn)), np.zeros((5, pc.g.Nn))
+    Jf, Jc = pf.jacobian(xf, gam_f), pc.jacobian(xc, gam_c)
+    P = MG.prolongation(pf.g, pc.g, pf.dmask, pc.dmask)
+    Ag = MG.galerkin(Jf, P, pc.dmask)
+    T = slice(4 * pc.g.Nn, 5 * pc.g.Nn)
+    assert abs(Ag[T, T] - Jc[T, T]).max() <= 1e-12 * abs(Jc[T, T]).max()
+    # and a wrong prolongation weight (1/4 instead of 1/2) breaks it
+    Pb = P.copy()
+    Pb.data[np.isclose(Pb.data, 0.5)] = 0.25
+    Ab = MG.galerkin(Jf, Pb, pc.dmask)
+    assert abs(Ab[T, T] - Jc[T, T]).max() > 1e-3 * abs(Jc[T, T]).max()
