@@ -1,13 +1,14 @@
 """One design iteration of an optimisation run, for timing and profiling.
 
-    python -m paper_1508_04596_gb300.design_iteration WORKLOAD [--fp64] [--no-adjoint]
+    python -m paper_1508_04596_gb300.design_iteration WORKLOAD [--fp64] [--no-adjoint] [--galerkin]
 
 Solves the state of the workload's design from a cold start, takes one
 synthetic optimiser step of the design (``synth.design_step``), then runs the
 warm-started Newton state solve, the objective, the adjoint solve and the
 element sensitivities (Sec. 3.2, Sec. 5) inside an NVTX range named "warm", so
 that a profiler can be restricted to it (``ncu --nvtx --nvtx-include warm/``).
-Prints the iteration counts and wall times of the warm part.
+Prints the iteration counts and wall times of the warm part.  With --galerkin the
+warm solves use Galerkin coarse operators (P^T A P) instead of rediscretised ones.
 """
 import argparse
 import json
@@ -23,6 +24,7 @@ def main(argv=None):
     ap.add_argument("workload")
     ap.add_argument("--fp64", action="store_true", help="plain FP64 instead of mixed precision")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--galerkin", action="store_true", help="Galerkin coarse operators")
     a = ap.parse_args(argv)
     mixed = 0 if a.fp64 else 1
     prob = nc.Problem.from_workload(a.workload, patch="flux")
@@ -32,7 +34,8 @@ def main(argv=None):
     x = torch.zeros(prob.ndof, dtype=torch.float64, device="cuda")
     prob.newton_solve(g0, x, nc.default_opts(mixed=1, ramp_steps=3))
     # load the kernels and allocate the workspace of this precision (untimed)
-    wopts = nc.default_opts(mixed=mixed, max_newton=1, max_lin=2)
+    gal = 1 if a.galerkin else 0
+    wopts = nc.default_opts(mixed=mixed, max_newton=1, max_lin=2, galerkin=gal)
     xw = x.clone()
     prob.newton_solve(g1, xw, wopts, check=False)
     _, dw = prob.objective(xw)
@@ -42,18 +45,20 @@ def main(argv=None):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("warm")
     t0 = time.perf_counter()
-    _, inf = prob.newton_solve(g1, x, nc.default_opts(mixed=mixed))
+    _, inf = prob.newton_solve(g1, x, nc.default_opts(mixed=mixed, galerkin=gal), check=False)
     torch.cuda.synchronize()
-    out = {"workload": a.workload, "mixed": mixed, "state_s": time.perf_counter() - t0,
-           "newton_its": inf["newton_its"], "lin_its": inf["lin_its_total"]}
+    out = {"workload": a.workload, "mixed": mixed, "galerkin": gal,
+           "state_s": time.perf_counter() - t0, "newton_its": inf["newton_its"],
+           "lin_its": inf["lin_its_total"], "state_status": inf["status"]}
     if not a.no_adjoint:
         t0 = time.perf_counter()
         phi, dphi = prob.objective(x)
-        lam, ainf = prob.adjoint_solve(x, g1, -dphi, opts=nc.default_opts(mixed=mixed))
+        lam, ainf = prob.adjoint_solve(x, g1, -dphi, opts=nc.default_opts(mixed=mixed, galerkin=gal),
+                                       check=False)
         prob.sensitivity(x, g1, lam)
         torch.cuda.synchronize()
         out.update(adjoint_plus_sens_s=time.perf_counter() - t0, phi=phi,
-                   adjoint_lin_its=ainf["lin_its_total"])
+                   adjoint_lin_its=ainf["lin_its_total"], adjoint_status=ainf["status"])
     torch.cuda.nvtx.range_pop()
     print(json.dumps(out))
 
