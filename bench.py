@@ -295,18 +295,42 @@ def run_ours(args, rank, world):
     outh = torch.empty((NAPPLY, ndof), dtype=dt).pin_memory()
     xd, gd, Vd, od = torch.empty_like(xj), torch.empty_like(gj), torch.empty_like(V), torch.empty_like(V)
 
+    # Copies overlap the products: the inputs stream in on one copy stream (x and
+    # gamma first, then each direction), each product waits only for its own
+    # direction, and its result streams out on a second copy stream while the
+    # next product runs.  Every step starts after the previous one has finished
+    # (its results are on the host), so buffers are reused safely.
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    ev_start = torch.cuda.Event()
+    ev_x = torch.cuda.Event()
+    ev_in = [torch.cuda.Event() for _ in range(NAPPLY)]
+    ev_done = [torch.cuda.Event() for _ in range(NAPPLY)]
+
     def e2e_step():
-        xd.copy_(xh, non_blocking=True)
-        gd.copy_(gh, non_blocking=True)
-        Vd.copy_(Vh, non_blocking=True)
+        ev_start.record(stream)
+        s_in.wait_event(ev_start)
+        s_out.wait_event(ev_start)
+        with torch.cuda.stream(s_in):
+            xd.copy_(xh, non_blocking=True)
+            gd.copy_(gh, non_blocking=True)
+            ev_x.record(s_in)
+            for i in range(NAPPLY):
+                Vd[i].copy_(Vh[i], non_blocking=True)
+                ev_in[i].record(s_in)
+        stream.wait_event(ev_x)
         if args.prec == "f64":
-            prob.linearize(xd, gd)
-            for i in range(NAPPLY):
-                prob.jvp_lin(Vd[i], od[i])
-        else:
-            for i in range(NAPPLY):
-                prob.jvp(xd, gd, Vd[i], od[i])
-        outh.copy_(od, non_blocking=True)
+            prob.linearize(xd, gd, stream=stream)
+        for i in range(NAPPLY):
+            stream.wait_event(ev_in[i])
+            if args.prec == "f64":
+                prob.jvp_lin(Vd[i], od[i], stream=stream)
+            else:
+                prob.jvp(xd, gd, Vd[i], od[i], stream=stream)
+            ev_done[i].record(stream)
+            s_out.wait_event(ev_done[i])
+            with torch.cuda.stream(s_out):
+                outh[i].copy_(od[i], non_blocking=True)
+        stream.wait_stream(s_out)
 
     for _ in range(2):
         e2e_step()
