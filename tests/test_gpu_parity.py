@@ -44,11 +44,14 @@ def host(t, shape=None):
     return a if shape is None else a.reshape(shape)
 
 
-# grids: cfg-0 cube, ragged non-cubic, flux patch
+# grids: cfg-0 cube, ragged non-cubic, flux patch, and the degenerate grids of one
+# element and of one element across
 CASES = [
     dict(nx=12, ny=12, nz=12, Gr=1e3, patch="dirichlet", seed=0),
     dict(nx=5, ny=7, nz=6, Gr=1e4, patch="flux", seed=1),
     dict(nx=9, ny=4, nz=3, Gr=1e5, patch="dirichlet", seed=2),
+    dict(nx=1, ny=1, nz=1, Gr=1e3, patch="dirichlet", seed=3),
+    dict(nx=2, ny=1, nz=3, Gr=1e4, patch="flux", seed=4),
 ]
 
 
@@ -252,10 +255,53 @@ def test_fins64_sampled_rows(nc, prec):
     JTw = host(gp.jtvp(dev(x, dt), dev(gam, dt), dev(v, dt)), (5, -1))
     nodes = rng.choice(prob.g.Nn, size=48, replace=False)
     vm = np.where(prob.dmask, 0.0, v)
-    for kind, got in (("jvp", Jv), ("jtvp", JTw)):
+    got_all = [("jvp", Jv), ("jtvp", JTw)]
+    if prec == "f64":  # the benchmark's FP64 step: linearisation store, then the products
+        X, Gm = dev(x), dev(gam)
+        gp.linearize(X, Gm)
+        got_all += [("jvp", host(gp.jvp_lin(dev(v)), (5, -1))),
+                    ("jtvp", host(gp.jtvp_lin(dev(v)), (5, -1)))]
+    for kind, got in got_all:
         ref = sampled_rows(prob.g, prob.prm, x, gam, vm, nodes, kind)
         ref = np.where(prob.dmask[:, nodes], v[:, nodes], ref)
         assert rel(got[:, nodes], ref) <= tol, kind
+
+
+def test_largest_config_sampled_rows(nc):
+    """192 x 192 x 384 (71.7M unknowns, the largest workload): J v and J^T w in FP32
+    (the operator of the mixed solves) and from the FP64 linearisation store (the
+    FP64 path) at 40 sampled nodes -- the corners, patch and top-face nodes and
+    random interior ones -- against element-by-element oracle rows."""
+    from oracle import element as El
+    from oracle import grid as G
+    from tests.helpers import oracle_bcs
+    name = "tall192x192x384_gr1e6"
+    cfg = synth.WORKLOADS[name]
+    g = G.Grid(cfg["nx"], cfg["ny"], cfg["nz"], cfg["h"])
+    m, dv = G.dirichlet(g, oracle_bcs(cfg["patch"]))
+    x = np.where(m, dv, synth.random_state(g.nx, g.ny, g.nz, 31, (0.5, 0.5, 0.5, 50, 1)))
+    gam = synth.design(name)
+    prm = El.Params(cfg["h"], cfg["Gr"], cfg["Pr"], **synth.MATERIAL)
+    rng = np.random.default_rng(32)
+    v = rng.standard_normal((5, g.Nn))
+    vm = np.where(m, 0.0, v)
+    nx1, ny1 = g.nx + 1, g.ny + 1
+    special = [0, g.nx, g.Nn - 1, g.Nn - nx1, g.node(96, 96, 0), g.node(64, 64, 0),
+               g.node(128, 128, 0), g.node(100, 90, 384), g.node(0, 96, 200), g.node(192, 5, 7)]
+    nodes = np.array(special + list(rng.choice(g.Nn, size=30, replace=False)))
+    gp = nc.Problem.from_workload(name)
+    refs = {k: np.where(m[:, nodes], v[:, nodes], sampled_rows(g, prm, x, gam, vm, nodes, k))
+            for k in ("jvp", "jtvp")}
+    X32, G32, V32 = dev(x, torch.float32), dev(gam, torch.float32), dev(v, torch.float32)
+    idx = torch.tensor(nodes, device="cuda")
+    pick = lambda t: host(t.view(5, -1)[:, idx])
+    assert rel(pick(gp.jvp(X32, G32, V32)), refs["jvp"]) <= TOL32
+    assert rel(pick(gp.jtvp(X32, G32, V32)), refs["jtvp"]) <= TOL32
+    del X32, G32, V32
+    X, Gm, V = dev(x), dev(gam), dev(v)
+    gp.linearize(X, Gm)
+    assert rel(pick(gp.jvp_lin(V)), refs["jvp"]) <= TOL64 * 10
+    assert rel(pick(gp.jtvp_lin(V)), refs["jtvp"]) <= TOL64 * 10
 
 
 def test_newton_matches_oracle_cfg0(nc):
