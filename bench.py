@@ -32,8 +32,8 @@ NAPPLY = 16  # J v applications per step
 # Operation counts per element (one +, -, * or / = 1 flop; an FMA = 2), of the
 # element routines in csrc/nc_element.cuh, counted by instantiating them with a
 # counting number type.
-FLOPS_PER_ELEM = {"residual": 2633, "jvp": 4345, "jtvp": 4466, "diag": 7272, "sens": 3797,
-                  "linearize": 1245, "jvp_lin": 3117}
+FLOPS_PER_ELEM = {"residual": 1893, "jvp": 3235, "jtvp": 3356, "diag": 7272, "sens": 3057,
+                  "linearize": 875, "jvp_lin": 2377}
 # ALU peaks (whole GPU): FP32 = 152 SM x 128 lanes x 2 flop x 2.07 GHz; FP64 = the
 # GB300's nominal 1.25 TFLOP/s (equal to our FMA-chain probe on the box: 78.5 and
 # 1.25 TFLOP/s measured).
@@ -279,7 +279,7 @@ def run_ours(args, rank, world):
     peak = ALU_PEAK_TFLOPS[args.prec]
     # DRAM bytes (read + write) of one element-kernel launch from the 128^3 ncu captures
     # of this kernel version (profiles/k_elem_lin_cavity128.md), scaled by elements
-    traffic = {"f64": 2743.35e6 + 949.11e6, "f32": 96.49e6 + 278.01e6}[args.prec] \
+    traffic = {"f64": 2757.53e6 + 1070.52e6, "f32": 96.49e6 + 278.16e6}[args.prec] \
         * prob.E / 2097152
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
             "unit": "TFLOP/s", "frac": round(achieved / peak, 4),

@@ -77,13 +77,13 @@ NC_HD constexpr double gfac(int i, int q) {
 }
 NC_HD constexpr double gsgn(int i) { return i ? 1.0 : -1.0; }
 
-// Interpolation to a pair of Gauss points.  The 8 points are processed in four
-// pairs (qy, qz) in {0,1}^2, each pair holding qx = 0 and qx = 1.  Along each
-// axis a Q1 field at a Gauss point is a linear interpolation x0 + c (x1 - x0)
-// with c = GW[q] (the shape-function weight of the "+" node), and the same
-// difference (x1 - x0) is the derivative along that axis, so values and
+// Along each axis a Q1 field at a Gauss point is a linear interpolation
+// x0 + c (x1 - x0) with c = GW[q] (the shape-function weight of the "+" node), and
+// the same difference (x1 - x0) is the derivative along that axis, so values and
 // gradients share their differences (a tensor-product factorisation of the
-// 2x2x2 rule).  Gradients carry 1/h.
+// 2x2x2 rule).  Gradients carry 1/h.  interp_pair takes one pair of points
+// (qy, qz fixed, qx = 0, 1); the diagonal of J uses it, every other element
+// routine takes all 8 points at once (interp8 below).
 constexpr double GW0 = 0.21132486540518711775;  // (1 - 1/sqrt 3)/2: weight of node 1 at point 0
 constexpr double GW1 = 0.78867513459481288225;  // (1 + 1/sqrt 3)/2: weight of node 1 at point 1
 NC_HD constexpr double gw(int q) { return q ? GW1 : GW0; }
@@ -110,47 +110,6 @@ NC_HD void interp_pair(const R x[8], R inv_h, R cy, R cz, R val[2], R& gx, R gy[
   const R ddz = zy1 - zy0;
   gz[0] = (zy0 + c0 * ddz) * inv_h;
   gz[1] = (zy0 + c1 * ddz) * inv_h;
-}
-
-// Transpose of interp_pair (without the 1/h, which the caller folds into F1):
-// out[a] += sum_qx [ N_a f0[qx] + dN_a/dxi_j F1[qx][j] ] over the pair.
-template <typename R>
-NC_HD void test_pair(R out[8], R cy, R cz, const R f0[2], const R F1[2][3]) {
-  const R c0 = R(GW0), c1 = R(GW1);
-  // cotangents of val[], gx, gy[], gz[]
-  const R gzb0 = F1[0][2], gzb1 = F1[1][2];
-  const R gyb0 = F1[0][1], gyb1 = F1[1][1];
-  const R gxb = F1[0][0] + F1[1][0];
-  // gz[q] = zy0 + c_q ddz ; ddz = zy1 - zy0
-  const R ddzb = c0 * gzb0 + c1 * gzb1;
-  const R zy0b = gzb0 + gzb1 - ddzb, zy1b = ddzb;
-  // gy[q] = dy0 + c_q ddy ; ddy = dy1 - dy0
-  const R ddyb = c0 * gyb0 + c1 * gyb1;
-  R dy0b = gyb0 + gyb1 - ddyb, dy1b = ddyb;
-  // val[q] = y0 + c_q dx ; gx = dx ; dx = y1 - y0
-  const R dxb = c0 * f0[0] + c1 * f0[1] + gxb;
-  const R y0b = f0[0] + f0[1] - dxb, y1b = dxb;
-  // y0 = z00 + cy dy0 ; y1 = z10 + cy dy1
-  dy0b += cy * y0b;
-  dy1b += cy * y1b;
-  // dy0 = z01 - z00 ; dy1 = z11 - z10
-  const R z00b = y0b - dy0b, z01b = dy0b, z10b = y1b - dy1b, z11b = dy1b;
-  // zy0 = dz00 + cy (dz01 - dz00) ; zy1 likewise
-  R dz00b = zy0b - cy * zy0b, dz01b = cy * zy0b, dz10b = zy1b - cy * zy1b, dz11b = cy * zy1b;
-  // z.. = x[..] + cz dz..
-  dz00b += cz * z00b;
-  dz10b += cz * z10b;
-  dz01b += cz * z01b;
-  dz11b += cz * z11b;
-  // dz.. = x[top] - x[bottom]
-  out[0] += z00b - dz00b;
-  out[1] += z10b - dz10b;
-  out[2] += z01b - dz01b;
-  out[3] += z11b - dz11b;
-  out[4] += dz00b;
-  out[5] += dz10b;
-  out[6] += dz01b;
-  out[7] += dz11b;
 }
 
 // Quadrature-point state: u, G[i][j] = d_j u_i, p, grad p, T, grad T.
@@ -208,18 +167,6 @@ NC_HD void interp_all_pair(const R xe[5][8], R inv_h, R cy, R cz, QP<R> q[2]) {
       q[s].gT[1] = g[s][1];
       q[s].gT[2] = g[s][2];
     }
-  }
-}
-
-// out[f] += test-side contributions of the pair for all five fields.
-template <typename R>
-NC_HD void test_all_pair(R out[5][8], R cy, R cz, const R f0[2][5], const R F1[2][5][3]) {
-#pragma unroll
-  for (int f = 0; f < 5; ++f) {
-    const R a[2] = {f0[0][f], f0[1][f]};
-    const R b[2][3] = {{F1[0][f][0], F1[0][f][1], F1[0][f][2]},
-                       {F1[1][f][0], F1[1][f][1], F1[1][f][2]}};
-    test_pair<R>(out[f], cy, cz, a, b);
   }
 }
 
@@ -313,50 +260,11 @@ NC_HD void flux_residual(const QP<R>& q, const ElemCoef<R>& k, const ElemConst<R
 }
 
 template <typename R>
-NC_HD void pair_residual(const R xe[5][8], const ElemCoef<R>& k, const ElemConst<R>& c, R cy,
-                         R cz, R out[5][8]) {
-  QP<R> q[2];
-  interp_all_pair<R>(xe, c.inv_h, cy, cz, q);
-  R f0[2][5], F1[2][5][3];
-  flux_residual(q[0], k, c, f0[0], F1[0]);
-  flux_residual(q[1], k, c, f0[1], F1[1]);
-  test_all_pair<R>(out, cy, cz, f0, F1);
-}
-
-// The four Gauss-point pairs (qy, qz), unrolled so that their weights are
-// compile-time constants (a rolled loop measured slower).
-#define NC_FOR_PAIRS(CALL)                           \
-  {                                                  \
-    const R cy = R(GW0), cz = R(GW0);                \
-    CALL;                                            \
-  }                                                  \
-  {                                                  \
-    const R cy = R(GW1), cz = R(GW0);                \
-    CALL;                                            \
-  }                                                  \
-  {                                                  \
-    const R cy = R(GW0), cz = R(GW1);                \
-    CALL;                                            \
-  }                                                  \
-  {                                                  \
-    const R cy = R(GW1), cz = R(GW1);                \
-    CALL;                                            \
-  }
-
-template <typename R>
 NC_HD void zero_out(R out[5][8]) {
 #pragma unroll
   for (int f = 0; f < 5; ++f)
 #pragma unroll
     for (int a = 0; a < 8; ++a) out[f][a] = R(0);
-}
-
-template <typename R>
-NC_HD void elem_residual(const R xe[5][8], R gam, R s, const ElemConst<R>& c, R out[5][8]) {
-  R S;
-  ElemCoef<R> k = elem_coef(xe, gam, s, c, S);
-  zero_out(out);
-  NC_FOR_PAIRS(pair_residual<R>(xe, k, c, cy, cz, out))
 }
 
 // ---------------------------------------------------------------------------- tangent
@@ -404,36 +312,6 @@ NC_HD void flux_tangent(const QP<R>& q, const QP<R>& d, const ElemCoef<R>& k, R 
   R body[3], rM[3], rT;
   strong(q, k, c, body, rM, rT);
   flux_tangent_rm<R, PARAM>(q, rM, rT, d, k, dalpha, dK, dtau, dtauT, c, f0, F1);
-}
-
-template <typename R>
-NC_HD void pair_jvp(const R xe[5][8], const R ve[5][8], const ElemCoef<R>& k, R dtau, R dtauT,
-                    const ElemConst<R>& c, R cy, R cz, R out[5][8]) {
-  QP<R> q[2], d[2];
-  interp_all_pair<R>(xe, c.inv_h, cy, cz, q);
-  interp_all_pair<R>(ve, c.inv_h, cy, cz, d);
-  R f0[2][5], F1[2][5][3];
-  flux_tangent<R, false>(q[0], d[0], k, R(0), R(0), dtau, dtauT, c, f0[0], F1[0]);
-  flux_tangent<R, false>(q[1], d[1], k, R(0), R(0), dtau, dtauT, c, f0[1], F1[1]);
-  test_all_pair<R>(out, cy, cz, f0, F1);
-}
-
-// J_e v_e including the dtau/du_e and dtau_T/du_e terms (App. B).
-template <typename R>
-NC_HD void elem_jvp(const R xe[5][8], const R ve[5][8], R gam, R s, const ElemConst<R>& c,
-                    R out[5][8]) {
-  R S;
-  ElemCoef<R> k = elem_coef(xe, gam, s, c, S);
-  R uv = R(0);
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int a = 0; a < 8; ++a) uv += xe[i][a] * ve[i][a];
-  // d tau = -1/2 tau^3 d(S/(16h^2)),  dS = 2 u_e.v_e
-  const R dtau = -k.tau * k.tau * k.tau * c.inv16h2 * uv;
-  const R dtauT = -k.tauT * k.tauT * k.tauT * c.inv16h2 * uv;
-  zero_out(out);
-  NC_FOR_PAIRS(pair_jvp<R>(xe, ve, k, dtau, dtauT, c, cy, cz, out))
 }
 
 // ---------------------------------------------------------------------------- adjoint
@@ -516,35 +394,6 @@ NC_HD void flux_adjoint(const QP<R>& q, const QP<R>& t, const ElemCoef<R>& k,
   flux_adjoint_rm(q, rM, rT, t, k, c, f0, F1, tau_bar, tauT_bar);
 }
 
-template <typename R>
-NC_HD void pair_jtvp(const R xe[5][8], const R we[5][8], const ElemCoef<R>& k,
-                     const ElemConst<R>& c, R cy, R cz, R out[5][8], R& tau_bar, R& tauT_bar) {
-  QP<R> q[2], t[2];
-  interp_all_pair<R>(xe, c.inv_h, cy, cz, q);
-  interp_all_pair<R>(we, c.inv_h, cy, cz, t);
-  R f0[2][5], F1[2][5][3];
-  flux_adjoint(q[0], t[0], k, c, f0[0], F1[0], tau_bar, tauT_bar);
-  flux_adjoint(q[1], t[1], k, c, f0[1], F1[1], tau_bar, tauT_bar);
-  test_all_pair<R>(out, cy, cz, f0, F1);
-}
-
-// J_e^T w_e.
-template <typename R>
-NC_HD void elem_jtvp(const R xe[5][8], const R we[5][8], R gam, R s, const ElemConst<R>& c,
-                     R out[5][8]) {
-  R S;
-  ElemCoef<R> k = elem_coef(xe, gam, s, c, S);
-  zero_out(out);
-  R tb = R(0), tbT = R(0);
-  NC_FOR_PAIRS(pair_jtvp<R>(xe, we, k, c, cy, cz, out, tb, tbT))
-  // tau(S), S = u_e^T u_e:  d tau/d u_e = -tau^3/(16 h^2) u_e  (App. B)
-  const R gsum = -(k.tau * k.tau * k.tau * tb + k.tauT * k.tauT * k.tauT * tbT) * (c.wq * c.inv16h2);
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int a = 0; a < 8; ++a) out[i][a] += gsum * xe[i][a];
-}
-
 // ---------------------------------------------------------------------------- design derivative
 template <typename R>
 NC_HD R point_sens(const QP<R>& q, const QP<R>& t, const ElemCoef<R>& k, R dalpha, R dK, R dtau,
@@ -570,31 +419,6 @@ NC_HD R point_sens(const QP<R>& q, const QP<R>& t, const ElemCoef<R>& k, R dalph
   return acc + acc1 * h;
 }
 
-template <typename R>
-NC_HD R pair_sens(const R xe[5][8], const R le[5][8], const ElemCoef<R>& k, R dalpha, R dK,
-                  R dtau, R dtauT, const ElemConst<R>& c, R cy, R cz) {
-  QP<R> q[2], t[2];
-  interp_all_pair<R>(xe, c.inv_h, cy, cz, q);
-  interp_all_pair<R>(le, c.inv_h, cy, cz, t);
-  return point_sens(q[0], t[0], k, dalpha, dK, dtau, dtauT, c) +
-         point_sens(q[1], t[1], k, dalpha, dK, dtau, dtauT, c);
-}
-
-// lambda_e^T d r_e / d gamma_e, through alpha_e, K_e, tau(alpha_e), tau_T(K_e).
-template <typename R>
-NC_HD R elem_sens(const R xe[5][8], const R le[5][8], R gam, R s, const ElemConst<R>& c) {
-  R S;
-  ElemCoef<R> k = elem_coef(xe, gam, s, c, S);
-  const R da = dalpha_of(gam, c), dK = dK_of(gam, c);
-  // tau^-2 = S/(16h^2) + tau2^-2 + alpha^2  ->  dtau = -tau^3 alpha dalpha
-  const R dtau = -k.tau * k.tau * k.tau * k.alpha * da;
-  // tau_T^-2 = S/(16h^2) + K^2 (4/h^2)^2   ->  dtau_T = -tau_T^3 K k2c dK
-  const R dtauT = -k.tauT * k.tauT * k.tauT * k.K * c.k2c * dK;
-  R acc = R(0);
-  NC_FOR_PAIRS(acc += pair_sens<R>(xe, le, k, da, dK, dtau, dtauT, c, cy, cz))
-  return acc;
-}
-
 // ---------------------------------------------------------------------------- linearisation cache
 // In a Krylov solve J is applied many times at one state.  The state-only part
 // of every Gauss point -- u, grad u, grad T and the strong residuals rM, rT --
@@ -606,45 +430,8 @@ NC_HD R elem_sens(const R xe[5][8], const R le[5][8], R gam, R s, const ElemCons
 constexpr int LIN_GP = 19;
 constexpr int LIN_SLOTS = 8 * LIN_GP + 2;
 
-template <typename R, int P>
-NC_HD void pair_linearize(const R xe[5][8], const ElemCoef<R>& k, const ElemConst<R>& c,
-                          R* cache, long long stride) {
-  QP<R> q[2];
-  interp_all_pair<R>(xe, c.inv_h, R(gw(P & 1)), R(gw(P >> 1)), q);
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    R conv[3], rM[3], rT;
-    strong(q[s], k, c, conv, rM, rT);
-    R* o = cache + (long long)((2 * P + s) * LIN_GP) * stride;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) o[i * stride] = q[s].u[i];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) o[(3 + 3 * i + j) * stride] = q[s].G[i][j];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) o[(12 + j) * stride] = q[s].gT[j];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) o[(15 + i) * stride] = rM[i];
-    o[18 * stride] = rT;
-  }
-}
-
 template <typename R>
-NC_HD void elem_linearize(const R xe[5][8], R gam, R s, const ElemConst<R>& c, R* cache,
-                          long long stride) {
-  R S;
-  ElemCoef<R> k = elem_coef(xe, gam, s, c, S);
-  pair_linearize<R, 0>(xe, k, c, cache, stride);
-  pair_linearize<R, 1>(xe, k, c, cache, stride);
-  pair_linearize<R, 2>(xe, k, c, cache, stride);
-  pair_linearize<R, 3>(xe, k, c, cache, stride);
-  cache[(long long)(8 * LIN_GP) * stride] = k.tau;
-  cache[(long long)(8 * LIN_GP + 1) * stride] = k.tauT;
-}
-
-template <typename R, int P>
-NC_HD void load_lin(const R* cache, long long stride, QP<R> q[2], R rM[2][3], R rT[2]) {
+NC_HD void load_lin_pair(const R* cache, long long stride, int P, QP<R> q[2], R rM[2][3], R rT[2]) {
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const R* o = cache + (long long)((2 * P + s) * LIN_GP) * stride;
@@ -659,7 +446,7 @@ NC_HD void load_lin(const R* cache, long long stride, QP<R> q[2], R rM[2][3], R 
 #pragma unroll
     for (int i = 0; i < 3; ++i) rM[s][i] = o[(15 + i) * stride];
     rT[s] = o[18 * stride];
-    q[s].p = q[s].T = R(0);  // not needed once rM, rT are known
+    q[s].p = q[s].T = R(0);
 #pragma unroll
     for (int i = 0; i < 3; ++i) q[s].gp[i] = R(0);
   }
@@ -675,74 +462,6 @@ NC_HD ElemCoef<R> lin_coef(const R* cache, long long stride, R gam, R s, const E
   k.s = s;
   scale_coef(k, c);
   return k;
-}
-
-template <typename R, int P>
-NC_HD void pair_jvp_lin(const R* cache, long long stride, const R ve[5][8], const ElemCoef<R>& k,
-                        R dtau, R dtauT, const ElemConst<R>& c, R out[5][8]) {
-  QP<R> q[2], d[2];
-  R rM[2][3], rT[2];
-  load_lin<R, P>(cache, stride, q, rM, rT);
-  const R cy = R(gw(P & 1)), cz = R(gw(P >> 1));
-  interp_all_pair<R>(ve, c.inv_h, cy, cz, d);
-  R f0[2][5], F1[2][5][3];
-  flux_tangent_rm<R, false>(q[0], rM[0], rT[0], d[0], k, R(0), R(0), dtau, dtauT, c, f0[0],
-                            F1[0]);
-  flux_tangent_rm<R, false>(q[1], rM[1], rT[1], d[1], k, R(0), R(0), dtau, dtauT, c, f0[1],
-                            F1[1]);
-  test_all_pair<R>(out, cy, cz, f0, F1);
-}
-
-// J_e v_e from the linearisation cache; ue holds the element's nodal velocities
-// (needed for dtau/du_e . v_e).
-template <typename R>
-NC_HD void elem_jvp_lin(const R* cache, long long stride, const R ue[3][8], const R ve[5][8],
-                        R gam, R s, const ElemConst<R>& c, R out[5][8]) {
-  const ElemCoef<R> k = lin_coef(cache, stride, gam, s, c);
-  R uv = R(0);
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int a = 0; a < 8; ++a) uv += ue[i][a] * ve[i][a];
-  const R dtau = -k.tau * k.tau * k.tau * c.inv16h2 * uv;
-  const R dtauT = -k.tauT * k.tauT * k.tauT * c.inv16h2 * uv;
-  zero_out(out);
-  pair_jvp_lin<R, 0>(cache, stride, ve, k, dtau, dtauT, c, out);
-  pair_jvp_lin<R, 1>(cache, stride, ve, k, dtau, dtauT, c, out);
-  pair_jvp_lin<R, 2>(cache, stride, ve, k, dtau, dtauT, c, out);
-  pair_jvp_lin<R, 3>(cache, stride, ve, k, dtau, dtauT, c, out);
-}
-
-template <typename R, int P>
-NC_HD void pair_jtvp_lin(const R* cache, long long stride, const R we[5][8],
-                         const ElemCoef<R>& k, const ElemConst<R>& c, R out[5][8], R& tau_bar,
-                         R& tauT_bar) {
-  QP<R> q[2], t[2];
-  R rM[2][3], rT[2];
-  load_lin<R, P>(cache, stride, q, rM, rT);
-  const R cy = R(gw(P & 1)), cz = R(gw(P >> 1));
-  interp_all_pair<R>(we, c.inv_h, cy, cz, t);
-  R f0[2][5], F1[2][5][3];
-  flux_adjoint_rm(q[0], rM[0], rT[0], t[0], k, c, f0[0], F1[0], tau_bar, tauT_bar);
-  flux_adjoint_rm(q[1], rM[1], rT[1], t[1], k, c, f0[1], F1[1], tau_bar, tauT_bar);
-  test_all_pair<R>(out, cy, cz, f0, F1);
-}
-
-template <typename R>
-NC_HD void elem_jtvp_lin(const R* cache, long long stride, const R ue[3][8], const R we[5][8],
-                         R gam, R s, const ElemConst<R>& c, R out[5][8]) {
-  const ElemCoef<R> k = lin_coef(cache, stride, gam, s, c);
-  zero_out(out);
-  R tb = R(0), tbT = R(0);
-  pair_jtvp_lin<R, 0>(cache, stride, we, k, c, out, tb, tbT);
-  pair_jtvp_lin<R, 1>(cache, stride, we, k, c, out, tb, tbT);
-  pair_jtvp_lin<R, 2>(cache, stride, we, k, c, out, tb, tbT);
-  pair_jtvp_lin<R, 3>(cache, stride, we, k, c, out, tb, tbT);
-  const R gsum = -(k.tau * k.tau * k.tau * tb + k.tauT * k.tauT * k.tauT * tbT) * (c.wq * c.inv16h2);
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int a = 0; a < 8; ++a) out[i][a] += gsum * ue[i][a];
 }
 
 // ---------------------------------------------------------------------------- diagonal
@@ -805,6 +524,338 @@ NC_HD void elem_diag(const R xe[5][8], R gam, R s, const ElemConst<R>& c, R out[
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int a = 0; a < 8; ++a) out[i][a] += dt * xe[i][a] * tc[i][a];
+}
+
+// ---------------------------------------------------------------------------- element routines
+// The tensor-product factorisation is taken over the whole element: per field,
+// the z stage (column differences and values at both qz), the y stage
+// (differences and values at both qy, and the z-difference interpolated in y)
+// and the x stage are each formed once for all 8 points (102 flop per field;
+// 176 when the points are taken pair by pair), and the test side is their exact
+// transpose (134 flop; 196 pair by pair).  Point index p = qx + 2 qy + 4 qz (the
+// order of the linearisation store).  All 8 points are live at once: more
+// local-memory traffic, fewer instructions, which measured faster in both
+// precisions.
+NC_HD constexpr int pt(int qx, int qy, int qz) { return qx + 2 * qy + 4 * qz; }
+
+// Values and (1/h-scaled) gradients of one Q1 field at the 8 Gauss points.
+template <typename R>
+NC_HD void interp8(const R x[8], R inv_h, R val[8], R g[8][3]) {
+  const R c[2] = {R(GW0), R(GW1)};
+  R dz[4], vz[2][4];
+#pragma unroll
+  for (int col = 0; col < 4; ++col) {  // column col = ia + 2 ja: nodes col, col + 4
+    dz[col] = x[col + 4] - x[col];
+    vz[0][col] = x[col] + c[0] * dz[col];
+    vz[1][col] = x[col] + c[1] * dz[col];
+  }
+  R dy[2][2], vyz[2][2][2];  // [qz][ia], [qz][qy][ia]
+#pragma unroll
+  for (int qz = 0; qz < 2; ++qz)
+#pragma unroll
+    for (int ia = 0; ia < 2; ++ia) {
+      dy[qz][ia] = vz[qz][ia + 2] - vz[qz][ia];
+      vyz[qz][0][ia] = vz[qz][ia] + c[0] * dy[qz][ia];
+      vyz[qz][1][ia] = vz[qz][ia] + c[1] * dy[qz][ia];
+    }
+  R dzy[2][2];  // z-difference interpolated in y: [qy][ia]
+#pragma unroll
+  for (int ia = 0; ia < 2; ++ia) {
+    const R ez = dz[ia + 2] - dz[ia];
+    dzy[0][ia] = dz[ia] + c[0] * ez;
+    dzy[1][ia] = dz[ia] + c[1] * ez;
+  }
+#pragma unroll
+  for (int qz = 0; qz < 2; ++qz)
+#pragma unroll
+    for (int qy = 0; qy < 2; ++qy) {
+      const R dx = vyz[qz][qy][1] - vyz[qz][qy][0];
+      const R gxv = dx * inv_h;
+#pragma unroll
+      for (int qx = 0; qx < 2; ++qx) {
+        val[pt(qx, qy, qz)] = vyz[qz][qy][0] + c[qx] * dx;
+        g[pt(qx, qy, qz)][0] = gxv;
+      }
+    }
+#pragma unroll
+  for (int qz = 0; qz < 2; ++qz) {
+    const R ey = dy[qz][1] - dy[qz][0];
+#pragma unroll
+    for (int qx = 0; qx < 2; ++qx) {
+      const R gyv = (dy[qz][0] + c[qx] * ey) * inv_h;
+      g[pt(qx, 0, qz)][1] = gyv;
+      g[pt(qx, 1, qz)][1] = gyv;
+    }
+  }
+#pragma unroll
+  for (int qy = 0; qy < 2; ++qy) {
+    const R ex = dzy[qy][1] - dzy[qy][0];
+#pragma unroll
+    for (int qx = 0; qx < 2; ++qx) {
+      const R gzv = (dzy[qy][0] + c[qx] * ex) * inv_h;
+      g[pt(qx, qy, 0)][2] = gzv;
+      g[pt(qx, qy, 1)][2] = gzv;
+    }
+  }
+}
+
+// Transpose of interp8 (without the 1/h, which the caller folds into F1):
+// out[a] += sum_p [ N_a(p) f0[p] + dN_a/dxi_j(p) F1[p][j] ].
+template <typename R>
+NC_HD void test8(R out[8], const R f0[8], const R F1[8][3]) {
+  const R c[2] = {R(GW0), R(GW1)};
+  R vyzb[2][2][2], dyb[2][2], dzyb[2][2];
+#pragma unroll
+  for (int qz = 0; qz < 2; ++qz)
+#pragma unroll
+    for (int qy = 0; qy < 2; ++qy) {
+      const int p0 = pt(0, qy, qz), p1 = pt(1, qy, qz);
+      const R dxb = c[0] * f0[p0] + c[1] * f0[p1] + (F1[p0][0] + F1[p1][0]);
+      vyzb[qz][qy][0] = f0[p0] + f0[p1] - dxb;
+      vyzb[qz][qy][1] = dxb;
+    }
+#pragma unroll
+  for (int qz = 0; qz < 2; ++qz) {
+    const R b0 = F1[pt(0, 0, qz)][1] + F1[pt(0, 1, qz)][1];
+    const R b1 = F1[pt(1, 0, qz)][1] + F1[pt(1, 1, qz)][1];
+    const R eyb = c[0] * b0 + c[1] * b1;
+    dyb[qz][0] = b0 + b1 - eyb;
+    dyb[qz][1] = eyb;
+  }
+#pragma unroll
+  for (int qy = 0; qy < 2; ++qy) {
+    const R b0 = F1[pt(0, qy, 0)][2] + F1[pt(0, qy, 1)][2];
+    const R b1 = F1[pt(1, qy, 0)][2] + F1[pt(1, qy, 1)][2];
+    const R exb = c[0] * b0 + c[1] * b1;
+    dzyb[qy][0] = b0 + b1 - exb;
+    dzyb[qy][1] = exb;
+  }
+  R vzb[2][4];
+#pragma unroll
+  for (int qz = 0; qz < 2; ++qz)
+#pragma unroll
+    for (int ia = 0; ia < 2; ++ia) {
+      const R d = dyb[qz][ia] + c[0] * vyzb[qz][0][ia] + c[1] * vyzb[qz][1][ia];
+      vzb[qz][ia] = vyzb[qz][0][ia] + vyzb[qz][1][ia] - d;
+      vzb[qz][ia + 2] = d;
+    }
+  R dzb[4];
+#pragma unroll
+  for (int ia = 0; ia < 2; ++ia) {
+    const R ezb = c[0] * dzyb[0][ia] + c[1] * dzyb[1][ia];
+    dzb[ia] = dzyb[0][ia] + dzyb[1][ia] - ezb;
+    dzb[ia + 2] = ezb;
+  }
+#pragma unroll
+  for (int col = 0; col < 4; ++col) {
+    const R d = dzb[col] + c[0] * vzb[0][col] + c[1] * vzb[1][col];
+    out[col] += vzb[0][col] + vzb[1][col] - d;
+    out[col + 4] += d;
+  }
+}
+
+template <typename R>
+NC_HD void interp_all8(const R xe[5][8], R inv_h, QP<R> q[8]) {
+  R val[8], g[8][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    interp8<R>(xe[i], inv_h, val, g);
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      q[p].u[i] = val[p];
+      q[p].G[i][0] = g[p][0];
+      q[p].G[i][1] = g[p][1];
+      q[p].G[i][2] = g[p][2];
+    }
+  }
+  interp8<R>(xe[3], inv_h, val, g);
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    q[p].p = val[p];
+    q[p].gp[0] = g[p][0];
+    q[p].gp[1] = g[p][1];
+    q[p].gp[2] = g[p][2];
+  }
+  interp8<R>(xe[4], inv_h, val, g);
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    q[p].T = val[p];
+    q[p].gT[0] = g[p][0];
+    q[p].gT[1] = g[p][1];
+    q[p].gT[2] = g[p][2];
+  }
+}
+
+template <typename R>
+NC_HD void test_all8(R out[5][8], const R f0[8][5], const R F1[8][5][3]) {
+#pragma unroll
+  for (int f = 0; f < 5; ++f) {
+    R a[8], b[8][3];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      a[p] = f0[p][f];
+      b[p][0] = F1[p][f][0];
+      b[p][1] = F1[p][f][1];
+      b[p][2] = F1[p][f][2];
+    }
+    test8<R>(out[f], a, b);
+  }
+}
+
+template <typename R>
+NC_HD void elem_residual(const R xe[5][8], R gam, R s, const ElemConst<R>& c, R out[5][8]) {
+  R S;
+  const ElemCoef<R> k = elem_coef(xe, gam, s, c, S);
+  QP<R> q[8];
+  interp_all8<R>(xe, c.inv_h, q);
+  R f0[8][5], F1[8][5][3];
+#pragma unroll
+  for (int p = 0; p < 8; ++p) flux_residual(q[p], k, c, f0[p], F1[p]);
+  zero_out(out);
+  test_all8<R>(out, f0, F1);
+}
+
+template <typename R>
+NC_HD void elem_jvp(const R xe[5][8], const R ve[5][8], R gam, R s, const ElemConst<R>& c,
+                     R out[5][8]) {
+  R S;
+  const ElemCoef<R> k = elem_coef(xe, gam, s, c, S);
+  R uv = R(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int a = 0; a < 8; ++a) uv += xe[i][a] * ve[i][a];
+  const R dtau = -k.tau * k.tau * k.tau * c.inv16h2 * uv;
+  const R dtauT = -k.tauT * k.tauT * k.tauT * c.inv16h2 * uv;
+  QP<R> q[8], d[8];
+  interp_all8<R>(xe, c.inv_h, q);
+  interp_all8<R>(ve, c.inv_h, d);
+  R f0[8][5], F1[8][5][3];
+#pragma unroll
+  for (int p = 0; p < 8; ++p)
+    flux_tangent<R, false>(q[p], d[p], k, R(0), R(0), dtau, dtauT, c, f0[p], F1[p]);
+  zero_out(out);
+  test_all8<R>(out, f0, F1);
+}
+
+template <typename R>
+NC_HD void elem_jtvp(const R xe[5][8], const R we[5][8], R gam, R s, const ElemConst<R>& c,
+                      R out[5][8]) {
+  R S;
+  const ElemCoef<R> k = elem_coef(xe, gam, s, c, S);
+  QP<R> q[8], t[8];
+  interp_all8<R>(xe, c.inv_h, q);
+  interp_all8<R>(we, c.inv_h, t);
+  R f0[8][5], F1[8][5][3];
+  R tb = R(0), tbT = R(0);
+#pragma unroll
+  for (int p = 0; p < 8; ++p) flux_adjoint(q[p], t[p], k, c, f0[p], F1[p], tb, tbT);
+  zero_out(out);
+  test_all8<R>(out, f0, F1);
+  const R gsum = -(k.tau * k.tau * k.tau * tb + k.tauT * k.tauT * k.tauT * tbT) * (c.wq * c.inv16h2);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int a = 0; a < 8; ++a) out[i][a] += gsum * xe[i][a];
+}
+
+template <typename R>
+NC_HD R elem_sens(const R xe[5][8], const R le[5][8], R gam, R s, const ElemConst<R>& c) {
+  R S;
+  const ElemCoef<R> k = elem_coef(xe, gam, s, c, S);
+  const R da = dalpha_of(gam, c), dK = dK_of(gam, c);
+  const R dtau = -k.tau * k.tau * k.tau * k.alpha * da;
+  const R dtauT = -k.tauT * k.tauT * k.tauT * k.K * c.k2c * dK;
+  QP<R> q[8], t[8];
+  interp_all8<R>(xe, c.inv_h, q);
+  interp_all8<R>(le, c.inv_h, t);
+  R acc = R(0);
+#pragma unroll
+  for (int p = 0; p < 8; ++p) acc += point_sens(q[p], t[p], k, da, dK, dtau, dtauT, c);
+  return acc;
+}
+
+template <typename R>
+NC_HD void elem_linearize(const R xe[5][8], R gam, R s, const ElemConst<R>& c, R* cache,
+                           long long stride) {
+  R S;
+  const ElemCoef<R> k = elem_coef(xe, gam, s, c, S);
+  QP<R> q[8];
+  interp_all8<R>(xe, c.inv_h, q);
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    R body[3], rM[3], rT;
+    strong(q[p], k, c, body, rM, rT);
+    R* o = cache + (long long)(p * LIN_GP) * stride;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o[i * stride] = q[p].u[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) o[(3 + 3 * i + j) * stride] = q[p].G[i][j];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) o[(12 + j) * stride] = q[p].gT[j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o[(15 + i) * stride] = rM[i];
+    o[18 * stride] = rT;
+  }
+  cache[(long long)(8 * LIN_GP) * stride] = k.tau;
+  cache[(long long)(8 * LIN_GP + 1) * stride] = k.tauT;
+}
+
+template <typename R>
+NC_HD void elem_jvp_lin(const R* cache, long long stride, const R ue[3][8], const R ve[5][8],
+                         R gam, R s, const ElemConst<R>& c, R out[5][8]) {
+  const ElemCoef<R> k = lin_coef(cache, stride, gam, s, c);
+  R uv = R(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int a = 0; a < 8; ++a) uv += ue[i][a] * ve[i][a];
+  const R dtau = -k.tau * k.tau * k.tau * c.inv16h2 * uv;
+  const R dtauT = -k.tauT * k.tauT * k.tauT * c.inv16h2 * uv;
+  QP<R> d[8];
+  interp_all8<R>(ve, c.inv_h, d);
+  R f0[8][5], F1[8][5][3];
+#pragma unroll
+  for (int P = 0; P < 4; ++P) {
+    QP<R> q[2];
+    R rM[2][3], rT[2];
+    load_lin_pair<R>(cache, stride, P, q, rM, rT);
+#pragma unroll
+    for (int sx = 0; sx < 2; ++sx)
+      flux_tangent_rm<R, false>(q[sx], rM[sx], rT[sx], d[2 * P + sx], k, R(0), R(0), dtau, dtauT,
+                                c, f0[2 * P + sx], F1[2 * P + sx]);
+  }
+  zero_out(out);
+  test_all8<R>(out, f0, F1);
+}
+
+template <typename R>
+NC_HD void elem_jtvp_lin(const R* cache, long long stride, const R ue[3][8], const R we[5][8],
+                          R gam, R s, const ElemConst<R>& c, R out[5][8]) {
+  const ElemCoef<R> k = lin_coef(cache, stride, gam, s, c);
+  QP<R> t[8];
+  interp_all8<R>(we, c.inv_h, t);
+  R f0[8][5], F1[8][5][3];
+  R tb = R(0), tbT = R(0);
+#pragma unroll
+  for (int P = 0; P < 4; ++P) {
+    QP<R> q[2];
+    R rM[2][3], rT[2];
+    load_lin_pair<R>(cache, stride, P, q, rM, rT);
+#pragma unroll
+    for (int sx = 0; sx < 2; ++sx)
+      flux_adjoint_rm(q[sx], rM[sx], rT[sx], t[2 * P + sx], k, c, f0[2 * P + sx], F1[2 * P + sx],
+                      tb, tbT);
+  }
+  zero_out(out);
+  test_all8<R>(out, f0, F1);
+  const R gsum = -(k.tau * k.tau * k.tau * tb + k.tauT * k.tauT * k.tauT * tbT) * (c.wq * c.inv16h2);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int a = 0; a < 8; ++a) out[i][a] += gsum * ue[i][a];
 }
 
 template <typename R>

@@ -15,6 +15,7 @@ constexpr int NODE_THREADS = 256;
 
 inline unsigned nblocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+
 __device__ __forceinline__ long long node_id(const LevelDev& d, int i, int j, int k) {
   return i + (long long)(d.nx + 1) * (j + (long long)(d.ny + 1) * k);
 }
@@ -72,10 +73,11 @@ __global__ void __launch_bounds__(ELEM_THREADS) k_elem_lin(LevelDev d, ElemConst
   R xe[5][8], ve[5][8], out[5][8];
   load_elem(d, x, e, xe, false);
   load_elem(d, v, e, ve, true);  // Dirichlet columns removed
+  const R g = gam[e], s = src ? src[e] : R(0);
   if (TRANSPOSE)
-    elem_jtvp<R>(xe, ve, gam[e], src ? src[e] : R(0), c, out);
+    elem_jtvp<R>(xe, ve, g, s, c, out);
   else
-    elem_jvp<R>(xe, ve, gam[e], src ? src[e] : R(0), c, out);
+    elem_jvp<R>(xe, ve, g, s, c, out);
   store_elem(d.E, e, out, Y);
 }
 
