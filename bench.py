@@ -8,7 +8,9 @@ Pr = 0.71 (the plain-FP64 GPU configuration).  One timed step is one batch of
 the reported value is J v throughput in GDOF/s (all 5 Nn unknowns per
 application).  The same run also times, outside the J v region, the full hot
 path once per precision: Newton state solve to 1e-8, adjoint solve to 1e-8 and
-the element sensitivities, FP32-mixed against plain FP64.
+the element sensitivities, FP32-mixed against plain FP64 (matrix-free, and
+with every level's Jacobian assembled into block stencils), and the build and
+product times of the assembled FP64 Jacobian at the J v state.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                        [--workload NAME] [--prec f64|f32] [--no-solve]
@@ -170,11 +172,11 @@ def run_ours(args, rank, world):
                                      "newton_its": cinf["newton_its"],
                                      "lin_its": cinf["lin_its_total"], "status": cinf["status"]}
         xs = {}
-        for mode, mixed in (("mixed", 1), ("fp64", 0)):
-            opts = nc.default_opts(mixed=mixed, rtol_newton=1e-8, ramp_steps=3)
+        for mode, mixed, assembled in (("mixed", 1, 0), ("fp64", 0, 0), ("fp64_assembled", 0, 1)):
+            opts = nc.default_opts(mixed=mixed, assembled=assembled, rtol_newton=1e-8, ramp_steps=3)
             # the first calls of a mode allocate its workspace and load its kernels:
             # one short untimed state and adjoint pass
-            wopts = nc.default_opts(mixed=mixed, max_newton=1, max_lin=2)
+            wopts = nc.default_opts(mixed=mixed, assembled=assembled, max_newton=1, max_lin=2)
             xw = x0.clone()
             sprob.newton_solve(sg1, xw, wopts, check=False)
             _, dw = sprob.objective(xw)
@@ -207,6 +209,14 @@ def run_ours(args, rank, world):
         solve["mixed_vs_fp64_sens_rel"] = float(torch.linalg.norm(sa - sb) / torch.linalg.norm(sb))
         solve["speedup_design_iteration"] = round(
             solve["fp64"]["design_iteration_s"] / solve["mixed"]["design_iteration_s"], 3)
+        xc, sc = xs["fp64_assembled"]
+        solve["fp64_assembled_vs_fp64_state_rel"] = float(torch.linalg.norm(xc - xb) / torch.linalg.norm(xb))
+        solve["fp64_assembled_vs_fp64_sens_rel"] = float(torch.linalg.norm(sc - sb) / torch.linalg.norm(sb))
+        solve["speedup_fp64_assembled_vs_fp64"] = round(
+            solve["fp64"]["design_iteration_s"] / solve["fp64_assembled"]["design_iteration_s"], 3)
+        solve["speedup_mixed_vs_fp64_assembled"] = round(
+            solve["fp64_assembled"]["design_iteration_s"] / solve["mixed"]["design_iteration_s"], 3)
+        del xs, xc, sa, sb, sc
         solve["workload"] = sw
         solve["objective"] = ("thermal compliance f = int s T dV (heat-source block)"
                               if synth.WORKLOADS[sw].get("bcs") == "quarter"
@@ -374,6 +384,9 @@ def run_ours(args, rank, world):
         ops[name] = {"ms": round(t, 4), "gdofs": round(ndof / t / 1e6, 3),
                      "alu_frac": round(FLOPS_PER_ELEM[base] * prob.E / (t * 1e-3) / 1e12 / pk, 4)}
     extra["operators"] = ops
+    extra["assembled"] = assembled_operator(
+        prob, x64, gam64, V.double(), ops["jvp"]["ms"],
+        t_step / NAPPLY if args.prec == "f64" else None, stream)
     extra["hbm_kernels"] = hbm_kernels(prob, stream)
     if solve:
         extra["solve"] = solve
@@ -393,6 +406,47 @@ def run_ours(args, rank, world):
             "roofline": roof, "cpu_baseline": cpu}
     line.update(extra)
     return line
+
+
+def assembled_operator(prob, x, gam, V, jvp_ms, jvp_lin_ms, stream, reps=5):
+    """The assembled FP64 Jacobian (nc_assemble) at the J v state: build time and
+    the throughput of its product (nc_stencil_apply, one k_stencil_apply launch),
+    against the matrix-free products (jvp_ms: nc_jvp; jvp_lin_ms: the benchmark
+    step's time per product, linearisation store included).  Per node the product reads 675 FP64
+    coefficients (5,400 B) and does 675 FMAs, so it is bound by the FP64 pipe
+    (1,350 flop per 5,480 B = 0.25 flop/B, above the 0.18 flop/B balance point)."""
+    import torch
+    S = torch.empty(675 * prob.Nn, dtype=torch.float64, device=x.device)
+    out = torch.empty_like(x)
+    prob.assemble(x, gam, S)
+    prob.stencil_apply(S, V[0], out)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        prob.assemble(x, gam, S)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_build = a.elapsed_time(b) / reps
+    a.record(stream)
+    for i in range(NAPPLY):
+        prob.stencil_apply(S, V[i], out)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_apply = a.elapsed_time(b) / NAPPLY
+    ta = t_apply * 1e-3
+    ref = jvp_lin_ms if jvp_lin_ms else jvp_ms
+    flops = 1350.0 * prob.Nn
+    nbytes = (5400.0 + 80.0) * prob.Nn
+    del S
+    return {"build_ms": round(t_build, 3), "apply_ms": round(t_apply, 4),
+            "gdofs": round(prob.ndof / ta / 1e9, 3),
+            "matrix_free_jvp_ms": jvp_ms, "matrix_free_jvp_lin_ms": jvp_lin_ms,
+            "alu_frac": round(flops / ta / 1e12 / ALU_PEAK_TFLOPS["f64"], 4),
+            "hbm_gbs": round(nbytes / ta / 1e9, 1),
+            "break_even_products": (round(t_build / (ref - t_apply), 1)
+                                    if ref > t_apply else None),
+            "kernel": "k_stencil_apply<double> (one thread per node, 27 x 5 x 5 FMAs)"}
 
 
 def hbm_kernels(prob, stream, n=5 * 129 ** 3, k=10, reps=10, only=None):

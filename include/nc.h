@@ -153,6 +153,25 @@ nc_status nc_jtvp_lin(nc_ctx* ctx, const double* w, double* JTw, void* stream);
 nc_status nc_diag(nc_ctx* ctx, const void* x, const void* gamma, void* d, int prec,
                   void* stream);
 
+/* Assembled Jacobian (the alternative to the matrix-free products): S receives
+ * J(x, gamma) as a 27-point stencil of 5 x 5 blocks,
+ *   S[((o*5 + f)*5 + g)*Nn + n] = dR(n, f) / dx(n + offset o, g),
+ *   o = (dx+1) + 3 (dy+1) + 9 (dz+1), dx, dy, dz in {-1, 0, 1},
+ * with entries reaching outside the grid 0, Dirichlet rows identity and
+ * Dirichlet columns 0 (the same blockdiag(J_II, I) as nc_jvp).  S: DEVICE,
+ * 675 Nn values of the precision prec, owned by the caller (5.4 KB per node in
+ * FP64).  Built from the element Jacobians: 40 element products with unit
+ * directions, each summed into S per node in a fixed order (deterministic); FP64
+ * first stores the linearisation (as nc_linearize, in a context-owned store
+ * allocated at the first call).  x and gamma as for nc_jvp. */
+nc_status nc_assemble(nc_ctx* ctx, const void* x, const void* gamma, void* S, int prec,
+                      void* stream);
+
+/* out = S v, or S^T v with transpose, for a stencil S from nc_assemble (one thread
+ * per node, neighbours in a fixed order).  v, out: [5][Nn] of the precision prec. */
+nc_status nc_stencil_apply(nc_ctx* ctx, const void* S, const void* v, void* out, int transpose,
+                           int prec, void* stream);
+
 /* Objective.  With patch_mode NC_PATCH_NONE and an element source set
  * (nc_set_source): the thermal compliance of Sec. 3.2, f = int_omega s T dV.
  * Otherwise: the mean temperature of the bottom patch,
@@ -227,6 +246,11 @@ typedef struct {
                           level above (the paper's choice, Sec. 5.2), built by probing once
                           per linearisation and applied as 27-point block stencils; 0
                           (default): rediscretised at the injected state and averaged design */
+  int assembled;       /* 1: every rediscretised level operator (level 0 included) is assembled
+                          once per linearisation into a 27-point block stencil (as nc_assemble)
+                          and applied as such; pays off in FP64 (mixed = 0), where an assembled
+                          product costs about a third of a matrix-free one; 0 (default):
+                          matrix-free */
 } nc_solve_opts;
 
 /* Per-solve report (Sec. 6.2 reports Newton and linear iteration counts). */
@@ -238,7 +262,7 @@ typedef struct {
 
 /* Fill opts with defaults (rtol_newton 1e-8, rtol_lin 1e-5, max_newton 30,
  * max_lin 200, restart 30, all levels, smooth_its 6, coarse_its 30, mixed 1,
- * ramp_steps 0, atol_newton 0, galerkin 0). */
+ * ramp_steps 0, atol_newton 0, galerkin 0, assembled 0). */
 void nc_default_opts(nc_solve_opts* opts);
 
 /* Damped Newton (Sec. 5.1) on R(x, gamma) = 0 from x_inout (Dirichlet values

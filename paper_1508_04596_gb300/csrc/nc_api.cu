@@ -174,6 +174,7 @@ void nc_destroy(nc_ctx* ctx) {
   cudaFree(ctx->cjel);
   for (auto& p : ctx->filt) cudaFree(p);
   cudaFree(ctx->pub_lin);
+  cudaFree(ctx->asm_lin);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
   delete ctx;
 }
@@ -373,6 +374,41 @@ nc_status nc_jtvp_lin(nc_ctx* ctx, const double* w, double* JTw, void* stream) {
   op_jtvp_cached<double>(L.d, L.c64, ctx->pub_x, ctx->pub_gam, L.f64.src, ctx->pub_lin, w, JTw,
                          ctx->Y, (cudaStream_t)stream);
   return cuda_check(ctx, cudaGetLastError(), "nc_jtvp_lin");
+}
+
+nc_status nc_assemble(nc_ctx* ctx, const void* x, const void* gam, void* S, int prec,
+                      void* stream) {
+  if (!ctx || !x || !gam || !S || !check_prec(prec))
+    return set_err(ctx, NC_ERR_ARG, "nc_assemble: bad argument");
+  const Level& L = ctx->lv[0];
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec == NC_FP64) {
+    nc_status st;
+    if (!ctx->asm_lin &&
+        (st = dev_alloc(ctx, &ctx->asm_lin, (long long)LIN_SLOTS * L.d.E)) != NC_OK)
+      return st;
+    op_linearize<double>(L.d, L.c64, (const double*)x, (const double*)gam, L.f64.src,
+                         ctx->asm_lin, s);
+    op_assemble<double>(L.d, L.c64, (const double*)x, (const double*)gam, L.f64.src,
+                        ctx->asm_lin, (double*)S, ctx->Y, s);
+  } else {
+    op_assemble<float>(L.d, L.c32, (const float*)x, (const float*)gam, L.f32.src, nullptr,
+                       (float*)S, (float*)ctx->Y, s);
+  }
+  return cuda_check(ctx, cudaGetLastError(), "nc_assemble");
+}
+
+nc_status nc_stencil_apply(nc_ctx* ctx, const void* S, const void* v, void* out, int transpose,
+                           int prec, void* stream) {
+  if (!ctx || !S || !v || !out || !check_prec(prec))
+    return set_err(ctx, NC_ERR_ARG, "nc_stencil_apply: bad argument");
+  const Level& L = ctx->lv[0];
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec == NC_FP64)
+    op_stencil<double>(L.d, (const double*)S, transpose != 0, (const double*)v, (double*)out, s);
+  else
+    op_stencil<float>(L.d, (const float*)S, transpose != 0, (const float*)v, (float*)out, s);
+  return cuda_check(ctx, cudaGetLastError(), "nc_stencil_apply");
 }
 
 nc_status nc_objective(nc_ctx* ctx, const double* x, double* phi_host, double* dphidx,

@@ -209,7 +209,7 @@ nc_status coarse_setup_stencil(nc_ctx* ctx, Level& L, const R* S, R** inv_dev, c
                          "cudaMalloc coarse inverse")) != NC_OK)
       return st;
   }
-  std::vector<R> sh((size_t)GALERKIN_STENCIL * Nn);
+  std::vector<R> sh((size_t)STENCIL_VALUES * Nn);
   if ((st = cuda_check(ctx, cudaMemcpyAsync(sh.data(), S, sizeof(R) * sh.size(),
                                             cudaMemcpyDeviceToHost, s), "coarse stencil D2H")) != NC_OK ||
       (st = cuda_check(ctx, cudaStreamSynchronize(s), "coarse sync")) != NC_OK)

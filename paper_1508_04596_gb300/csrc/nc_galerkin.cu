@@ -1,5 +1,7 @@
-// Galerkin-projection coarse operators (Sec. 5.2): A_c = P^T A_f P on every
-// coarse level, stored as a 27-point stencil of 5 x 5 blocks per node.
+// Operators stored as a 27-point stencil of 5 x 5 blocks per node: the
+// assembled Jacobian of a level (built from the element Jacobians in
+// nc_kernels.cu) and the Galerkin-projection coarse operators of Sec. 5.2,
+// A_c = P^T A_f P on every coarse level.
 //
 // P is the trilinear prolongation of the V-cycle (fine Dirichlet unknowns left
 // at zero) and P^T its restriction (fine Dirichlet rows dropped, coarse
@@ -153,7 +155,7 @@ void galerkin_probe_scatter(const LevelDev& d, int c, int g, const R* r, R* S, c
 }
 
 template <typename R>
-void galerkin_dirichlet(const LevelDev& d, R* S, cudaStream_t s) {
+void stencil_dirichlet(const LevelDev& d, R* S, cudaStream_t s) {
   k_stencil_dirichlet<R><<<gblocks(d.Nn), GT, 0, s>>>(d, S);
 }
 
@@ -162,7 +164,7 @@ void galerkin_dirichlet(const LevelDev& d, R* S, cudaStream_t s) {
   template void op_stencil_diag<R>(const LevelDev&, const R*, R*, cudaStream_t);                \
   template void galerkin_probe_init<R>(const LevelDev&, int, int, R*, cudaStream_t);            \
   template void galerkin_probe_scatter<R>(const LevelDev&, int, int, const R*, R*, cudaStream_t);\
-  template void galerkin_dirichlet<R>(const LevelDev&, R*, cudaStream_t);
+  template void stencil_dirichlet<R>(const LevelDev&, R*, cudaStream_t);
 NC_INST(double)
 NC_INST(float)
 #undef NC_INST

@@ -93,6 +93,7 @@ struct nc_ctx {
   cudaStream_t cap = nullptr; // stream used to capture the V-cycle graph
   double* filt[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // filter CG
   double* pub_lin = nullptr;  // linearisation of nc_linearize (level 0, FP64)
+  double* asm_lin = nullptr;  // linearisation used by nc_assemble (level 0, FP64)
   const double* pub_x = nullptr;
   const double* pub_gam = nullptr;
   std::string err;
@@ -208,9 +209,16 @@ template <typename R>
 void vcombine(long long n, int k, const R* X, long long ld, const double* coef, const R* D, R* z,
               bool accumulate, cudaStream_t s);
 
-// ---- Galerkin coarse operators (nc_galerkin.cu): S holds 675 * Nn entries,
-// S[((o*5 + f)*5 + g)*Nn + n] couples (n, f) to (n + offset o, g)
-constexpr int GALERKIN_STENCIL = 675;
+// ---- stencil operators (nc_galerkin.cu): assembled level operators and Galerkin
+// coarse operators.  S holds 675 * Nn entries, S[((o*5 + f)*5 + g)*Nn + n] couples
+// (n, f) to (n + offset o, g), o = (dx+1) + 3 (dy+1) + 9 (dz+1)
+constexpr int STENCIL_VALUES = 675;
+// S = J(x, gamma) of one level, from its element Jacobians (nc_kernels.cu): 40
+// element products with unit directions (reading `cache` when not null), each
+// summed into S per node; Dirichlet rows identity, Dirichlet columns zero.
+template <typename R>
+void op_assemble(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam, const R* src,
+                 const R* cache, R* S, R* Y, cudaStream_t s);
 template <typename R>
 void op_stencil(const LevelDev& d, const R* S, bool tr, const R* v, R* out, cudaStream_t s);
 template <typename R>
@@ -220,7 +228,7 @@ void galerkin_probe_init(const LevelDev& d, int c, int g, R* v, cudaStream_t s);
 template <typename R>
 void galerkin_probe_scatter(const LevelDev& d, int c, int g, const R* r, R* S, cudaStream_t s);
 template <typename R>
-void galerkin_dirichlet(const LevelDev& d, R* S, cudaStream_t s);
+void stencil_dirichlet(const LevelDev& d, R* S, cudaStream_t s);
 
 // ---- coarsest-level direct solve (nc_coarse.cu)
 constexpr int COARSE_DENSE_MAX = 1000;  // largest coarsest level solved by a dense inverse

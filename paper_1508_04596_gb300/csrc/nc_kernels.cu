@@ -41,6 +41,29 @@ __device__ __forceinline__ void load_elem(const LevelDev& d, const R* __restrict
   }
 }
 
+// node of local index a (bit 0: +x, bit 1: +y, bit 2: +z) of element e
+__device__ __forceinline__ long long elem_node(const LevelDev& d, long long e, int a) {
+  const int i = (int)(e % d.nx);
+  const long long t = e / d.nx;
+  const int j = (int)(t % d.ny);
+  const int k = (int)(t / d.ny);
+  return node_id(d, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+}
+
+// nodal velocities of the state (the only state data the cached products read)
+template <typename R>
+__device__ __forceinline__ void load_vel(const LevelDev& d, const R* __restrict__ x, long long e,
+                                         R ue[3][8]) {
+  const long long n0 = elem_node(d, e, 0);
+  const long long sy = d.nx + 1, sz = (long long)(d.nx + 1) * (d.ny + 1);
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const long long n = n0 + (a & 1) + ((a >> 1) & 1) * sy + ((a >> 2) & 1) * sz;
+#pragma unroll
+    for (int f = 0; f < 3; ++f) ue[f][a] = x[f * d.Nn + n];
+  }
+}
+
 template <typename R>
 __device__ __forceinline__ void store_elem(long long E, long long e, const R out[5][8], R* Y) {
 #pragma unroll
@@ -103,20 +126,7 @@ __global__ void __launch_bounds__(ELEM_THREADS) k_elem_lin_cached(
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= d.E) return;
   R ue[3][8], ve[5][8], out[5][8];
-  {
-    const int i = (int)(e % d.nx);
-    const long long t = e / d.nx;
-    const int j = (int)(t % d.ny);
-    const int k = (int)(t / d.ny);
-    const long long n0 = node_id(d, i, j, k);
-    const long long sy = d.nx + 1, sz = (long long)(d.nx + 1) * (d.ny + 1);
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const long long n = n0 + (a & 1) + ((a >> 1) & 1) * sy + ((a >> 2) & 1) * sz;
-#pragma unroll
-      for (int f = 0; f < 3; ++f) ue[f][a] = x[f * d.Nn + n];
-    }
-  }
+  load_vel(d, x, e, ue);
   load_elem(d, v, e, ve, true);  // Dirichlet columns removed
   const R g = gam[e], s = src ? src[e] : R(0);
   if (TRANSPOSE)
@@ -124,6 +134,75 @@ __global__ void __launch_bounds__(ELEM_THREADS) k_elem_lin_cached(
   else
     elem_jvp_lin<R>(cache + e, d.E, ue, ve, g, s, c, out);
   store_elem(d.E, e, out, Y);
+}
+
+// Column col = 5 b + g of every element Jacobian: the element product with the
+// unit direction on unknown g of local node b, or zero where that unknown is
+// Dirichlet (Dirichlet columns are removed).  With a linearisation cache the
+// product reads it, else it re-interpolates the state.
+template <typename R, bool CACHED>
+__global__ void __launch_bounds__(ELEM_THREADS) k_elem_column(
+    LevelDev d, ElemConst<R> c, const R* __restrict__ x, const R* __restrict__ gam,
+    const R* __restrict__ src, const R* __restrict__ cache, int col, R* Y) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= d.E) return;
+  const int b = col / 5, g = col % 5;
+  R out[5][8];
+  if ((d.flag[elem_node(d, e, b)] >> g) & 1) {
+#pragma unroll
+    for (int f = 0; f < 5; ++f)
+#pragma unroll
+      for (int a = 0; a < 8; ++a) out[f][a] = R(0);
+    store_elem(d.E, e, out, Y);
+    return;
+  }
+  R ve[5][8];
+#pragma unroll
+  for (int f = 0; f < 5; ++f)
+#pragma unroll
+    for (int a = 0; a < 8; ++a) ve[f][a] = (f == g && a == b) ? R(1) : R(0);
+  const R gm = gam[e], s = src ? src[e] : R(0);
+  if (CACHED) {
+    R ue[3][8];
+    load_vel(d, x, e, ue);
+    elem_jvp_lin<R>(cache + e, d.E, ue, ve, gm, s, c, out);
+  } else {
+    R xe[5][8];
+    load_elem(d, x, e, xe, false);
+    elem_jvp<R>(xe, ve, gm, s, c, out);
+  }
+  store_elem(d.E, e, out, Y);
+}
+
+// S += column col = 5 b + g of the element Jacobians, summed per node: row (n, f)
+// takes entry (f, a) of each element e around n (n is e's local node a), at the
+// stencil offset of e's local node b from n.  The eight elements around n give
+// eight distinct offsets, so one launch writes no entry twice; the launches run
+// in column order, so the sums are deterministic.  Dirichlet rows are skipped
+// (they become identity rows afterwards).
+template <typename R>
+__global__ void __launch_bounds__(NODE_THREADS) k_assemble_column(LevelDev d, int col,
+                                                                  const R* __restrict__ Y,
+                                                                  R* __restrict__ S) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= d.Nn) return;
+  const int i = (int)(n % (d.nx + 1));
+  const long long t = n / (d.nx + 1);
+  const int j = (int)(t % (d.ny + 1));
+  const int k = (int)(t / (d.ny + 1));
+  const int b = col / 5, g = col % 5;
+  const uint8_t fl = d.flag[n];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int ie = i - (a & 1), je = j - ((a >> 1) & 1), ke = k - ((a >> 2) & 1);
+    if (ie < 0 || je < 0 || ke < 0 || ie >= d.nx || je >= d.ny || ke >= d.nz) continue;
+    const long long e = ie + (long long)d.nx * (je + (long long)d.ny * ke);
+    const int o = ((b & 1) - (a & 1) + 1) + 3 * (((b >> 1) & 1) - ((a >> 1) & 1) + 1) +
+                  9 * (((b >> 2) & 1) - ((a >> 2) & 1) + 1);
+#pragma unroll
+    for (int f = 0; f < 5; ++f)
+      if (!((fl >> f) & 1)) S[((long long)(o * 5 + f) * 5 + g) * d.Nn + n] += Y[(f * 8 + a) * d.E + e];
+  }
 }
 
 template <typename R>
@@ -402,6 +481,22 @@ void op_diag(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam,
   k_gather<R, G_DIAG><<<nblocks(d.Nn, NODE_THREADS), NODE_THREADS, 0, s>>>(d, Y, x, out);
 }
 
+template <typename R>
+void op_assemble(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam, const R* src,
+                 const R* cache, R* S, R* Y, cudaStream_t s) {
+  cudaMemsetAsync(S, 0, sizeof(R) * (size_t)STENCIL_VALUES * (size_t)d.Nn, s);
+  for (int col = 0; col < 40; ++col) {
+    if (cache)
+      k_elem_column<R, true><<<nblocks(d.E, ELEM_THREADS), ELEM_THREADS, 0, s>>>(d, c, x, gam, src,
+                                                                               cache, col, Y);
+    else
+      k_elem_column<R, false><<<nblocks(d.E, ELEM_THREADS), ELEM_THREADS, 0, s>>>(d, c, x, gam, src,
+                                                                                nullptr, col, Y);
+    k_assemble_column<R><<<nblocks(d.Nn, NODE_THREADS), NODE_THREADS, 0, s>>>(d, col, Y, S);
+  }
+  stencil_dirichlet<R>(d, S, s);
+}
+
 void op_sens(const LevelDev& d, const ElemConst<double>& c, const double* x, const double* gam,
              const double* src, const double* lam, double* out, cudaStream_t s) {
   k_elem_sens<<<nblocks(d.E, ELEM_THREADS), ELEM_THREADS, 0, s>>>(d, c, x, gam, src, lam, out);
@@ -469,6 +564,8 @@ void op_coarsen_elem(const LevelDev& fine, const R* gf, const LevelDev& coarse, 
                                  const R*, const R*, const R*, R*, R*, cudaStream_t);           \
   template void op_jtvp_cached<R>(const LevelDev&, const ElemConst<R>&, const R*, const R*,     \
                                   const R*, const R*, const R*, R*, R*, cudaStream_t);          \
+  template void op_assemble<R>(const LevelDev&, const ElemConst<R>&, const R*, const R*,        \
+                               const R*, const R*, R*, R*, cudaStream_t);                       \
   template void op_impose<R>(const LevelDev&, R*, cudaStream_t);                                \
   template void op_mask<R>(const LevelDev&, R*, cudaStream_t);                                  \
   template void op_restrict<R>(const LevelDev&, const R*, const LevelDev&, R*, cudaStream_t);   \

@@ -110,7 +110,7 @@ template <typename R>
 void level_apply(nc_ctx* ctx, int l, bool tr, const R* v, R* out, cudaStream_t s) {
   Level& L = ctx->lv[l];
   LevelBuf<R>& B = buf<R>(L);
-  if (l > 0 && B.use_gst) {  // Galerkin coarse operator
+  if (B.use_gst) {  // assembled or Galerkin operator
     op_stencil<R>(L.d, B.gst, tr, v, out, s);
     return;
   }
@@ -208,8 +208,8 @@ nc_status alloc_levels(nc_ctx* ctx, int nlev, const nc_solve_opts& o) {
     if (sizeof(R) == sizeof(double) &&
         (st = alloc(ctx, &B.lin, (long long)LIN_SLOTS * L.d.E)) != NC_OK)
       return st;
-    if (o.galerkin && l >= 1 &&
-        (st = alloc(ctx, &B.gst, (long long)GALERKIN_STENCIL * L.d.Nn)) != NC_OK)
+    if ((o.assembled || (o.galerkin && l >= 1)) &&
+        (st = alloc(ctx, &B.gst, (long long)STENCIL_VALUES * L.d.Nn)) != NC_OK)
       return st;
     const bool level0_f64 = (l == 0) && sizeof(R) == sizeof(double);
     if (!level0_f64) {
@@ -238,16 +238,19 @@ void galerkin_build(nc_ctx* ctx, int l, cudaStream_t s) {
       op_restrict<R>(F.d, (const R*)BF.r, L.d, BL.r, s);
       galerkin_probe_scatter<R>(L.d, c, g, (const R*)BL.r, BL.gst, s);
     }
-  galerkin_dirichlet<R>(L.d, BL.gst, s);
+  stencil_dirichlet<R>(L.d, BL.gst, s);
 }
 
 // Linearisation data of every level in precision R at (x, gamma) (FP64 inputs):
 // level 0 is x, gamma themselves (FP64) or their FP32 casts; coarser levels take
 // the injected state and the mean design of the eight children and are
-// rediscretised there, or (galerkin) hold P^T A P of the level above; then diag(J).
+// rediscretised there, or (galerkin) hold P^T A P of the level above; with
+// assembled, every rediscretised level's operator is assembled into a stencil;
+// then diag(J).
 template <typename R>
 nc_status linearize(nc_ctx* ctx, int nlev, const double* x, const double* gam, cudaStream_t s,
-                    bool galerkin) {
+                    const nc_solve_opts& o) {
+  const bool galerkin = o.galerkin != 0, assembled = o.assembled != 0;
   for (int l = 0; l < nlev; ++l) {
     Level& L = ctx->lv[l];
     LevelBuf<R>& B = buf<R>(L);
@@ -265,9 +268,13 @@ nc_status linearize(nc_ctx* ctx, int nlev, const double* x, const double* gam, c
       op_inject<R>(F.d, buf<R>(F).x, L.d, B.x, s);
       op_coarsen_elem<R>(F.d, buf<R>(F).gam, L.d, B.gam, s);
     }
-    B.use_gst = galerkin && l >= 1;
-    if (B.use_gst) {
+    B.use_gst = assembled || (galerkin && l >= 1);
+    if (galerkin && l >= 1) {
       galerkin_build<R>(ctx, l, s);
+      op_stencil_diag<R>(L.d, B.gst, B.diag, s);
+    } else if (assembled) {
+      if (B.lin) op_linearize<R>(L.d, cst<R>(L), B.x, B.gam, B.src, B.lin, s);
+      op_assemble<R>(L.d, cst<R>(L), B.x, B.gam, B.src, B.lin, B.gst, (R*)ctx->Y, s);
       op_stencil_diag<R>(L.d, B.gst, B.diag, s);
     } else {
       // diag(J^T) = diag(J)
@@ -598,8 +605,8 @@ nc_status newton(nc_ctx* ctx, const double* gam, double* x, const nc_solve_opts&
       info->res_final = nr;
       return set_err(ctx, NC_ERR_MAXIT, "Newton reached max_newton");
     }
-    st = mixed ? linearize<float>(ctx, nlev, x, gam, s, o.galerkin != 0)
-               : linearize<double>(ctx, nlev, x, gam, s, o.galerkin != 0);
+    st = mixed ? linearize<float>(ctx, nlev, x, gam, s, o)
+               : linearize<double>(ctx, nlev, x, gam, s, o);
     if (st != NC_OK) return st;
     // J d = R, the Newton step is -d
     int lits = 0;
@@ -666,6 +673,7 @@ void nc_default_opts(nc_solve_opts* o) {
   o->ramp_steps = 0;
   o->atol_newton = 0.0;
   o->galerkin = 0;
+  o->assembled = 0;
 }
 
 nc_status nc_newton_solve(nc_ctx* ctx, const double* gam, double* x, const nc_solve_opts* opts,
@@ -793,8 +801,8 @@ nc_status nc_mg_apply(nc_ctx* ctx, int level, const double* x, const double* gam
   const bool mixed = prec == NC_FP32;
   nc_status st = prepare(ctx, o, nlev, mixed);
   if (st != NC_OK) return st;
-  st = mixed ? linearize<float>(ctx, nlev, x, gam, s, o.galerkin != 0)
-             : linearize<double>(ctx, nlev, x, gam, s, o.galerkin != 0);
+  st = mixed ? linearize<float>(ctx, nlev, x, gam, s, o)
+             : linearize<double>(ctx, nlev, x, gam, s, o);
   if (st == NC_OK) {
     if (mixed)
       level_apply<float>(ctx, level, transpose != 0, (const float*)v, (float*)out, s);
@@ -841,8 +849,8 @@ nc_status nc_adjoint_solve(nc_ctx* ctx, const double* x, const double* gam, cons
     while (st == NC_OK && nr > o.rtol_newton * nb && nr > 0.0) {
       if (k >= o.max_newton) { st = set_err(ctx, NC_ERR_MAXIT, "adjoint refinement limit"); break; }
       if (!linearized) {
-        st = mixed ? linearize<float>(ctx, nlev, x, gam, s, o.galerkin != 0)
-                   : linearize<double>(ctx, nlev, x, gam, s, o.galerkin != 0);
+        st = mixed ? linearize<float>(ctx, nlev, x, gam, s, o)
+                   : linearize<double>(ctx, nlev, x, gam, s, o);
         if (st != NC_OK) break;
         linearized = true;
       }

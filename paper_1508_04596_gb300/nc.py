@@ -50,7 +50,8 @@ class SolveOpts(ctypes.Structure):
                 ("restart", ctypes.c_int), ("mg_levels", ctypes.c_int),
                 ("smooth_its", ctypes.c_int), ("coarse_its", ctypes.c_int),
                 ("mixed", ctypes.c_int), ("ramp_steps", ctypes.c_int),
-                ("atol_newton", ctypes.c_double), ("galerkin", ctypes.c_int)]
+                ("atol_newton", ctypes.c_double), ("galerkin", ctypes.c_int),
+                ("assembled", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -93,6 +94,8 @@ _SIGS = {
     "nc_default_opts": (None, [ctypes.POINTER(SolveOpts)]),
     "nc_filter": (ctypes.c_int, [_ctx, _vp, _vp, ctypes.c_double, _vp]),
     "nc_linearize": (ctypes.c_int, [_ctx, _vp, _vp, _vp]),
+    "nc_assemble": (ctypes.c_int, [_ctx, _vp, _vp, _vp, ctypes.c_int, _vp]),
+    "nc_stencil_apply": (ctypes.c_int, [_ctx, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp]),
     "nc_jvp_lin": (ctypes.c_int, [_ctx, _vp, _vp, _vp]),
     "nc_jtvp_lin": (ctypes.c_int, [_ctx, _vp, _vp, _vp]),
     "nc_newton_solve": (ctypes.c_int, [_ctx, _vp, _vp, ctypes.POINTER(SolveOpts),
@@ -263,6 +266,30 @@ class Problem:
         self._chk(lib.nc_jtvp(self.ctx, self._vec(x, dt, self.ndof, "x"),
                               self._vec(gam, dt, self.E, "gamma"), self._vec(w, dt, self.ndof, "w"),
                               self._vec(out, dt, self.ndof, "JTw"), self._prec(x), _stream(stream)))
+        return out
+
+    STENCIL_VALUES = 675
+
+    def assemble(self, x, gam, S=None, stream=None):
+        """The Jacobian J(x, gamma) assembled as a 27-point stencil of 5 x 5 blocks:
+        S[((o*5 + f)*5 + g)*Nn + n] couples (n, f) to (n + offset o, g), with
+        o = (dx+1) + 3 (dy+1) + 9 (dz+1); 675 Nn values of x's dtype."""
+        dt = x.dtype
+        n = self.STENCIL_VALUES * self.Nn
+        S = torch.empty(n, dtype=dt, device=x.device) if S is None else S
+        self._chk(lib.nc_assemble(self.ctx, self._vec(x, dt, self.ndof, "x"),
+                                  self._vec(gam, dt, self.E, "gamma"), self._vec(S, dt, n, "S"),
+                                  self._prec(x), _stream(stream)))
+        return S
+
+    def stencil_apply(self, S, v, out=None, transpose=False, stream=None):
+        """out = S v (or S^T v) for a stencil from assemble()."""
+        dt = v.dtype
+        out = torch.empty_like(v) if out is None else out
+        self._chk(lib.nc_stencil_apply(self.ctx, self._vec(S, dt, self.STENCIL_VALUES * self.Nn, "S"),
+                                       self._vec(v, dt, self.ndof, "v"),
+                                       self._vec(out, dt, self.ndof, "out"), int(transpose),
+                                       self._prec(v), _stream(stream)))
         return out
 
     def arnoldi_orth(self, V, w, k, ldv, stream=None):
