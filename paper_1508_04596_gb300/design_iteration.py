@@ -1,6 +1,7 @@
 """One design iteration of an optimisation run, for timing and profiling.
 
     python -m paper_1508_04596_gb300.design_iteration WORKLOAD [--fp64] [--no-adjoint] [--galerkin]
+                                                      [--assembled]
 
 Solves the state of the workload's design from a cold start, takes one
 synthetic optimiser step of the design (``synth.design_step``), then runs the
@@ -25,6 +26,8 @@ def main(argv=None):
     ap.add_argument("--fp64", action="store_true", help="plain FP64 instead of mixed precision")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--galerkin", action="store_true", help="Galerkin coarse operators")
+    ap.add_argument("--assembled", action="store_true",
+                    help="assemble every level's Jacobian into a block stencil")
     a = ap.parse_args(argv)
     mixed = 0 if a.fp64 else 1
     prob = nc.Problem.from_workload(a.workload, patch="flux")
@@ -35,7 +38,8 @@ def main(argv=None):
     prob.newton_solve(g0, x, nc.default_opts(mixed=1, ramp_steps=3))
     # load the kernels and allocate the workspace of this precision (untimed)
     gal = 1 if a.galerkin else 0
-    wopts = nc.default_opts(mixed=mixed, max_newton=1, max_lin=2, galerkin=gal)
+    asm = 1 if a.assembled else 0
+    wopts = nc.default_opts(mixed=mixed, max_newton=1, max_lin=2, galerkin=gal, assembled=asm)
     xw = x.clone()
     prob.newton_solve(g1, xw, wopts, check=False)
     _, dw = prob.objective(xw)
@@ -45,15 +49,15 @@ def main(argv=None):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("warm")
     t0 = time.perf_counter()
-    _, inf = prob.newton_solve(g1, x, nc.default_opts(mixed=mixed, galerkin=gal), check=False)
+    _, inf = prob.newton_solve(g1, x, nc.default_opts(mixed=mixed, galerkin=gal, assembled=asm), check=False)
     torch.cuda.synchronize()
-    out = {"workload": a.workload, "mixed": mixed, "galerkin": gal,
+    out = {"workload": a.workload, "mixed": mixed, "galerkin": gal, "assembled": asm,
            "state_s": time.perf_counter() - t0, "newton_its": inf["newton_its"],
            "lin_its": inf["lin_its_total"], "state_status": inf["status"]}
     if not a.no_adjoint:
         t0 = time.perf_counter()
         phi, dphi = prob.objective(x)
-        lam, ainf = prob.adjoint_solve(x, g1, -dphi, opts=nc.default_opts(mixed=mixed, galerkin=gal),
+        lam, ainf = prob.adjoint_solve(x, g1, -dphi, opts=nc.default_opts(mixed=mixed, galerkin=gal, assembled=asm),
                                        check=False)
         prob.sensitivity(x, g1, lam)
         torch.cuda.synchronize()
