@@ -522,9 +522,14 @@ def oracle_sample(workload, layers=4):
     return prob, gam, x
 
 
-def cpu_baseline(workload, reps=16):
-    """Oracle J v as an assembled CSR SpMV (scipy, one thread) on a bounded sample."""
+def cpu_baseline(workload, reps=16, newton=True):
+    """Oracle J v as an assembled CSR SpMV (scipy, one thread) on a bounded sample,
+    plus the oracle's residual evaluation on the same sample and its Newton + sparse
+    direct (SuperLU) solve of the 12^3 heated cavity to 1e-10."""
     prob, gam, x = oracle_sample(workload)
+    t0 = time.perf_counter()
+    prob.residual(x, gam)
+    t_res = time.perf_counter() - t0
     t0 = time.perf_counter()
     J = prob.jacobian(x, gam)
     t_asm = time.perf_counter() - t0
@@ -533,10 +538,25 @@ def cpu_baseline(workload, reps=16):
     for _ in range(reps):
         J @ v
     t = (time.perf_counter() - t0) / reps
-    return {"value": round(prob.g.ndof / t / 1e9, 5), "unit": "GDOF/s", "cores": 1,
-            "kind": "oracle",
-            "sample": "%dx%dx%d bottom layers of %s: complex-step CSR assembly %.1f s, then %d SpMV"
-                      % (prob.g.nx, prob.g.ny, prob.g.nz, workload, t_asm, reps)}
+    out = {"value": round(prob.g.ndof / t / 1e9, 5), "unit": "GDOF/s", "cores": 1,
+           "kind": "oracle",
+           "sample": "%dx%dx%d bottom layers of %s: complex-step CSR assembly %.1f s, then %d SpMV"
+                     % (prob.g.nx, prob.g.ny, prob.g.nz, workload, t_asm, reps),
+           "residual_gdofs": round(prob.g.ndof / t_res / 1e9, 6),
+           "cpu_count": os.cpu_count(),
+           "affinity": len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else None}
+    if newton:
+        from oracle import solve as S
+        from paper_1508_04596_gb300 import synth
+        from tests.helpers import oracle_problem
+        name = "cavity12_gr1e3"
+        cfg = synth.WORKLOADS[name]
+        p, _ = oracle_problem(cfg["nx"], cfg["ny"], cfg["nz"], cfg["h"], cfg["Gr"], cfg["Pr"])
+        t0 = time.perf_counter()
+        _, its = S.newton(p, synth.design(name), np.zeros((5, p.g.Nn)), rtol=1e-10)
+        out["newton_splu_12cube_s"] = round(time.perf_counter() - t0, 2)
+        out["newton_splu_12cube_its"] = int(its)
+    return out
 
 
 def run_reference(args, rank, world):
