@@ -2,6 +2,8 @@
 
     python -m paper_1508_04596_gb300.optimize WORKLOAD [--iters N] [--steps S]
                                                        [--nx NX --ny NY --nz NZ] [--fp64]
+                                                       [--checkpoint PATH [--every K]]
+                                                       [--resume PATH]
 
 Per design iteration: the PDE density filter of the design variables, the
 passive elements reset (solid heat-source block, fluid outside the design
@@ -19,6 +21,12 @@ continuation (Sec. 3.3):
 with the iterations split evenly over the steps (the paper runs 500 or 1000
 iterations in total and does not give the split).  Every numerical step runs
 in libnc's kernels; this module only orders the calls.
+
+Checkpoint / resume: the run's whole state (design variables, the MMA history
+and asymptotes, the last converged state that warm-starts the next Newton
+solve, the iteration counter and the objective scaling) is saved with
+torch.save every K iterations and at the end; a resumed run continues from it
+and, the kernels being deterministic, gives the same iterates bit for bit.
 """
 import argparse
 import json
@@ -76,6 +84,34 @@ class Optimizer:
         self.x = None
         self.f0_scale = None
 
+    _TENSORS = ("rho", "xold1", "xold2", "low", "upp", "x")
+
+    def state_dict(self):
+        """Everything a resumed run needs, as host tensors and plain values."""
+        d = {k: getattr(self, k).detach().cpu() for k in self._TENSORS if getattr(self, k) is not None}
+        d.update(workload=self.workload, over=dict(self.over), vf=self.vf, move=self.move,
+                 mixed=self.mixed, state_rtol=self.state_rtol, adjoint_rtol=self.adjoint_rtol,
+                 k=self.k, step=self.step, f0_scale=self.f0_scale)
+        return d
+
+    def save(self, path):
+        torch.save(self.state_dict(), path)
+
+    @classmethod
+    def load(cls, path):
+        d = torch.load(path, map_location="cpu", weights_only=True)
+        opt = cls(d["workload"], vf=d["vf"], move=d["move"], mixed=d["mixed"],
+                  state_rtol=d["state_rtol"], adjoint_rtol=d["adjoint_rtol"], **d["over"])
+        for k in cls._TENSORS:
+            if k in d:
+                setattr(opt, k, d[k].to("cuda"))
+        opt.k, opt.f0_scale = d["k"], d["f0_scale"]
+        if d["step"] >= 0:
+            x = opt.x
+            opt.set_step(d["step"])
+            opt.x = x
+        return opt
+
     def set_step(self, step):
         """Material parameters of continuation step `step` (a new context; the
         state and the MMA history carry over)."""
@@ -125,17 +161,22 @@ class Optimizer:
                 "s": round(time.perf_counter() - t0, 4)}
 
 
-def run(workload, iters, steps=5, log=print, **kw):
-    """`iters` design iterations over the first `steps` continuation steps."""
-    opt = Optimizer(workload, **kw)
+def run(workload, iters, steps=5, log=print, checkpoint=None, every=10, resume=None, **kw):
+    """`iters` design iterations in total over the first `steps` continuation
+    steps; with `resume`, continue the run saved there (its iterations count
+    towards `iters`); with `checkpoint`, save the run there every `every`
+    iterations and at the end."""
+    opt = Optimizer.load(resume) if resume else Optimizer(workload, **kw)
     per = max(1, iters // steps)
     hist = []
-    for it in range(iters):
-        opt.set_step(min(it // per, steps - 1, len(CONTINUATION) - 1))
+    while opt.k < iters:
+        opt.set_step(min(opt.k // per, steps - 1, len(CONTINUATION) - 1))
         r = opt.iterate()
         hist.append(r)
         if log:
             log(json.dumps(r))
+        if checkpoint and (opt.k % every == 0 or opt.k == iters):
+            opt.save(checkpoint)
     return opt, hist
 
 
@@ -148,13 +189,17 @@ def main(argv=None):
     ap.add_argument("--ny", type=int)
     ap.add_argument("--nz", type=int)
     ap.add_argument("--fp64", action="store_true")
+    ap.add_argument("--checkpoint", help="save the run here (every --every iterations and at the end)")
+    ap.add_argument("--every", type=int, default=10)
+    ap.add_argument("--resume", help="continue the run saved in this file")
     a = ap.parse_args(argv)
     over = {}
     if a.nx:
         cfg = synth.WORKLOADS[a.workload]
         over = dict(nx=a.nx, ny=a.ny or a.nx, nz=a.nz or a.nx)
         over["h"] = cfg["h"] * cfg["nz"] / over["nz"]
-    run(a.workload, a.iters, a.steps, mixed=0 if a.fp64 else 1, **over)
+    run(a.workload, a.iters, a.steps, checkpoint=a.checkpoint, every=a.every, resume=a.resume,
+        mixed=0 if a.fp64 else 1, **over)
 
 
 if __name__ == "__main__":
