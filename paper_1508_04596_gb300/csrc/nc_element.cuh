@@ -858,6 +858,136 @@ NC_HD void elem_jtvp_lin(const R* cache, long long stride, const R ue[3][8], con
     for (int a = 0; a < 8; ++a) out[i][a] += gsum * ue[i][a];
 }
 
+// ---------------------------------------------------------------------------- element columns
+// Pointwise tangent fluxes for a unit direction on one unknown of one node: phi
+// = N_b and psi = grad N_b at the point, on unknown G (0-2 a velocity component,
+// 3 the pressure, 4 the temperature).  The same terms as flux_tangent_rm with
+// every product by a zero of the direction left out; dtau, dtauT are zero for
+// G >= 3 (tau depends on the velocities only).
+template <typename R, int G>
+NC_HD void flux_column(const QP<R>& q, const R rM[3], R rT, R phi, const R psi[3],
+                       const ElemCoef<R>& k, R whdtau, R whdtauT, const ElemConst<R>& c, R f0[5],
+                       R F1[5][3]) {
+  const R w = c.wq;
+  if (G < 3) {
+    const R upsi = q.u[0] * psi[0] + q.u[1] * psi[1] + q.u[2] * psi[2];
+    R a[3], b[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      R body = phi * q.G[i][G];  // d.u . grad u_i
+      if (i == G) body += upsi + k.alpha * phi;
+      f0[i] = w * body;
+      a[i] = whdtau * rM[i] + k.wtau * body;
+      b[i] = k.wtau * rM[i];
+      F1[3][i] = a[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        R t = q.u[j] * a[i];
+        if (i == j && i == G) t += c.prw2 * psi[i];
+        if (i != j && i == G) t += c.prw * psi[j];
+        if (i != j && j == G) t += c.prw * psi[i];
+        if (j == G) t += phi * b[i];
+        F1[i][j] = t;
+      }
+    const R drT = phi * q.gT[G];
+    f0[3] = w * psi[G];
+    f0[4] = w * drT;
+    const R aT = whdtauT * rT + k.wtauT * drT, bT = k.wtauT * rT;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) F1[4][j] = j == G ? q.u[j] * aT + phi * bT : q.u[j] * aT;
+  } else if (G == 3) {
+    R a[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      f0[i] = R(0);
+      a[i] = k.wtau * psi[i];
+      F1[3][i] = a[i];
+    }
+    const R pw = c.wh * phi;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) F1[i][j] = i == j ? q.u[j] * a[i] - pw : q.u[j] * a[i];
+    f0[3] = f0[4] = R(0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) F1[4][j] = R(0);
+  } else {
+    R a[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const R body = c.beg[i] * phi;
+      f0[i] = w * body;
+      a[i] = k.wtau * body;
+      F1[3][i] = a[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) F1[i][j] = q.u[j] * a[i];
+    const R drT = q.u[0] * psi[0] + q.u[1] * psi[1] + q.u[2] * psi[2];
+    f0[3] = R(0);
+    f0[4] = w * drT;
+    const R aT = k.wtauT * drT;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) F1[4][j] = k.wK * psi[j] + q.u[j] * aT;
+  }
+}
+
+// Column (b, G) of the element Jacobian from the linearisation store: the
+// product elem_jvp_lin with the unit direction on unknown G of local node b.
+// The direction's interpolation is N_b and grad N_b at the points in closed
+// form (products of the 1-D weights), and flux_column forms only the nonzero
+// tangent terms; the test side is the full one.
+// ub: the state's velocity component G at node b (unused for G >= 3).
+template <typename R, int G>
+NC_HD void elem_column_lin(const R* cache, long long stride, R ub, int b, R gam, R s,
+                           const ElemConst<R>& c, R out[5][8]) {
+  const ElemCoef<R> k = lin_coef(cache, stride, gam, s, c);
+  R whdtau = R(0), whdtauT = R(0);
+  if (G < 3) {  // d(u_e^T u_e)/2 along the direction = u_e(G, b)
+    whdtau = c.wh * (-k.tau * k.tau * k.tau * c.inv16h2 * ub);
+    whdtauT = c.wh * (-k.tauT * k.tauT * k.tauT * c.inv16h2 * ub);
+  }
+  const R W[2] = {R(GW0), R(GW1)};  // weight of node bit 1 at point bit 0 / 1
+  const int bx = b & 1, by = (b >> 1) & 1, bz = (b >> 2) & 1;
+  const R sx = bx ? c.inv_h : -c.inv_h, sy = by ? c.inv_h : -c.inv_h,
+          sz = bz ? c.inv_h : -c.inv_h;
+  R f0[8][5], F1[8][5][3];
+#pragma unroll
+  for (int P = 0; P < 4; ++P) {
+    QP<R> q[2];
+    R rM[2][3], rT[2];
+    load_lin_pair<R>(cache, stride, P, q, rM, rT);
+#pragma unroll
+    for (int qx = 0; qx < 2; ++qx) {
+      const int p = 2 * P + qx, qy = P & 1, qz = P >> 1;
+      const R lx = bx ? W[qx] : R(1) - W[qx];
+      const R ly = by ? W[qy] : R(1) - W[qy];
+      const R lz = bz ? W[qz] : R(1) - W[qz];
+      const R psi[3] = {sx * (ly * lz), sy * (lx * lz), sz * (lx * ly)};
+      flux_column<R, G>(q[qx], rM[qx], rT[qx], lx * ly * lz, psi, k, whdtau, whdtauT, c, f0[p],
+                        F1[p]);
+    }
+  }
+  zero_out(out);
+#pragma unroll
+  for (int f = 0; f < 5; ++f) {
+    if (G == 3 && f == 4) continue;  // the energy rows do not see the pressure
+    R a0[8], b0[8][3];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      a0[p] = f0[p][f];
+      b0[p][0] = F1[p][f][0];
+      b0[p][1] = F1[p][f][1];
+      b0[p][2] = F1[p][f][2];
+    }
+    test8<R>(out[f], a0, b0);
+  }
+}
+
 template <typename R>
 NC_HD ElemConst<R> make_const(double h, double Gr, double Pr, double amax, double qa, double qf,
                               double Ck, const double eg[3]) {

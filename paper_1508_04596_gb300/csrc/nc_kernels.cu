@@ -138,12 +138,11 @@ __global__ void __launch_bounds__(ELEM_THREADS) k_elem_lin_cached(
 
 // Column col = 5 b + g of every element Jacobian: the element product with the
 // unit direction on unknown g of local node b, or zero where that unknown is
-// Dirichlet (Dirichlet columns are removed).  With a linearisation cache the
-// product reads it, else it re-interpolates the state.
-template <typename R, bool CACHED>
+// Dirichlet (Dirichlet columns are removed).  Re-interpolates the state.
+template <typename R>
 __global__ void __launch_bounds__(ELEM_THREADS) k_elem_column(
     LevelDev d, ElemConst<R> c, const R* __restrict__ x, const R* __restrict__ gam,
-    const R* __restrict__ src, const R* __restrict__ cache, int col, R* Y) {
+    const R* __restrict__ src, int col, R* Y) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= d.E) return;
   const int b = col / 5, g = col % 5;
@@ -156,20 +155,34 @@ __global__ void __launch_bounds__(ELEM_THREADS) k_elem_column(
     store_elem(d.E, e, out, Y);
     return;
   }
-  R ve[5][8];
+  R ve[5][8], xe[5][8];
 #pragma unroll
   for (int f = 0; f < 5; ++f)
 #pragma unroll
     for (int a = 0; a < 8; ++a) ve[f][a] = (f == g && a == b) ? R(1) : R(0);
-  const R gm = gam[e], s = src ? src[e] : R(0);
-  if (CACHED) {
-    R ue[3][8];
-    load_vel(d, x, e, ue);
-    elem_jvp_lin<R>(cache + e, d.E, ue, ve, gm, s, c, out);
+  load_elem(d, x, e, xe, false);
+  elem_jvp<R>(xe, ve, gam[e], src ? src[e] : R(0), c, out);
+  store_elem(d.E, e, out, Y);
+}
+
+// The same column from the linearisation store with the unit direction written
+// out (elem_column_lin): unknown G, local node b.
+template <typename R, int G>
+__global__ void __launch_bounds__(ELEM_THREADS) k_elem_column_lin(
+    LevelDev d, ElemConst<R> c, const R* __restrict__ x, const R* __restrict__ gam,
+    const R* __restrict__ src, const R* __restrict__ cache, int b, R* Y) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= d.E) return;
+  R out[5][8];
+  const long long nb = elem_node(d, e, b);
+  if ((d.flag[nb] >> G) & 1) {
+#pragma unroll
+    for (int f = 0; f < 5; ++f)
+#pragma unroll
+      for (int a = 0; a < 8; ++a) out[f][a] = R(0);
   } else {
-    R xe[5][8];
-    load_elem(d, x, e, xe, false);
-    elem_jvp<R>(xe, ve, gm, s, c, out);
+    const R ub = G < 3 ? x[G * d.Nn + nb] : R(0);
+    elem_column_lin<R, G>(cache + e, d.E, ub, b, gam[e], src ? src[e] : R(0), c, out);
   }
   store_elem(d.E, e, out, Y);
 }
@@ -485,13 +498,19 @@ template <typename R>
 void op_assemble(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam, const R* src,
                  const R* cache, R* S, R* Y, cudaStream_t s) {
   cudaMemsetAsync(S, 0, sizeof(R) * (size_t)STENCIL_VALUES * (size_t)d.Nn, s);
+  const unsigned eb = nblocks(d.E, ELEM_THREADS);
   for (int col = 0; col < 40; ++col) {
-    if (cache)
-      k_elem_column<R, true><<<nblocks(d.E, ELEM_THREADS), ELEM_THREADS, 0, s>>>(d, c, x, gam, src,
-                                                                               cache, col, Y);
-    else
-      k_elem_column<R, false><<<nblocks(d.E, ELEM_THREADS), ELEM_THREADS, 0, s>>>(d, c, x, gam, src,
-                                                                                nullptr, col, Y);
+    const int b = col / 5;
+    if (cache) {
+      switch (col % 5) {
+        case 0: k_elem_column_lin<R, 0><<<eb, ELEM_THREADS, 0, s>>>(d, c, x, gam, src, cache, b, Y); break;
+        case 1: k_elem_column_lin<R, 1><<<eb, ELEM_THREADS, 0, s>>>(d, c, x, gam, src, cache, b, Y); break;
+        case 2: k_elem_column_lin<R, 2><<<eb, ELEM_THREADS, 0, s>>>(d, c, x, gam, src, cache, b, Y); break;
+        case 3: k_elem_column_lin<R, 3><<<eb, ELEM_THREADS, 0, s>>>(d, c, x, gam, src, cache, b, Y); break;
+        default: k_elem_column_lin<R, 4><<<eb, ELEM_THREADS, 0, s>>>(d, c, x, gam, src, cache, b, Y);
+      }
+    } else
+      k_elem_column<R><<<eb, ELEM_THREADS, 0, s>>>(d, c, x, gam, src, col, Y);
     k_assemble_column<R><<<nblocks(d.Nn, NODE_THREADS), NODE_THREADS, 0, s>>>(d, col, Y, S);
   }
   stencil_dirichlet<R>(d, S, s);
