@@ -1,7 +1,7 @@
 """One design iteration of an optimisation run, for timing and profiling.
 
     python -m paper_1508_04596_gb300.design_iteration WORKLOAD [--fp64] [--no-adjoint] [--galerkin]
-                                                      [--assembled]
+                                                      [--assembled] [--restart M]
 
 Solves the state of the workload's design from a cold start, takes one
 synthetic optimiser step of the design (``synth.design_step``), then runs the
@@ -28,18 +28,26 @@ def main(argv=None):
     ap.add_argument("--galerkin", action="store_true", help="Galerkin coarse operators")
     ap.add_argument("--assembled", action="store_true",
                     help="assemble every level's Jacobian into a block stencil")
+    ap.add_argument("--restart", type=int, default=30, help="FGMRES restart (memory: 2 vectors each)")
     a = ap.parse_args(argv)
     mixed = 0 if a.fp64 else 1
     prob = nc.Problem.from_workload(a.workload, patch="flux")
-    g0 = torch.tensor(synth.design(a.workload), dtype=torch.float64, device="cuda")
-    g1 = torch.tensor(synth.design_step(a.workload, synth.design(a.workload), 77),
-                      dtype=torch.float64, device="cuda")
+    gh = synth.design(a.workload)
+    g0 = torch.tensor(gh, dtype=torch.float64, device="cuda")
+    g1 = torch.tensor(synth.design_step(a.workload, gh, 77), dtype=torch.float64, device="cuda")
+    del gh
     x = torch.zeros(prob.ndof, dtype=torch.float64, device="cuda")
-    prob.newton_solve(g0, x, nc.default_opts(mixed=1, ramp_steps=3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, cinf = prob.newton_solve(g0, x, nc.default_opts(mixed=1, ramp_steps=3, restart=a.restart))
+    torch.cuda.synchronize()
+    cold = {"cold_state_s": time.perf_counter() - t0, "cold_newton_its": cinf["newton_its"],
+            "cold_lin_its": cinf["lin_its_total"]}
     # load the kernels and allocate the workspace of this precision (untimed)
     gal = 1 if a.galerkin else 0
     asm = 1 if a.assembled else 0
-    wopts = nc.default_opts(mixed=mixed, max_newton=1, max_lin=2, galerkin=gal, assembled=asm)
+    kw = dict(mixed=mixed, galerkin=gal, assembled=asm, restart=a.restart)
+    wopts = nc.default_opts(max_newton=1, max_lin=2, **kw)
     xw = x.clone()
     prob.newton_solve(g1, xw, wopts, check=False)
     _, dw = prob.objective(xw)
@@ -49,7 +57,7 @@ def main(argv=None):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("warm")
     t0 = time.perf_counter()
-    _, inf = prob.newton_solve(g1, x, nc.default_opts(mixed=mixed, galerkin=gal, assembled=asm), check=False)
+    _, inf = prob.newton_solve(g1, x, nc.default_opts(**kw), check=False)
     torch.cuda.synchronize()
     out = {"workload": a.workload, "mixed": mixed, "galerkin": gal, "assembled": asm,
            "state_s": time.perf_counter() - t0, "newton_its": inf["newton_its"],
@@ -57,13 +65,15 @@ def main(argv=None):
     if not a.no_adjoint:
         t0 = time.perf_counter()
         phi, dphi = prob.objective(x)
-        lam, ainf = prob.adjoint_solve(x, g1, -dphi, opts=nc.default_opts(mixed=mixed, galerkin=gal, assembled=asm),
-                                       check=False)
+        lam, ainf = prob.adjoint_solve(x, g1, -dphi, opts=nc.default_opts(**kw), check=False)
         prob.sensitivity(x, g1, lam)
         torch.cuda.synchronize()
         out.update(adjoint_plus_sens_s=time.perf_counter() - t0, phi=phi,
                    adjoint_lin_its=ainf["lin_its_total"], adjoint_status=ainf["status"])
     torch.cuda.nvtx.range_pop()
+    free, total = torch.cuda.mem_get_info()
+    out.update(cold, dof=prob.ndof, restart=a.restart,
+               device_mem_used_gb=round((total - free) / 1e9, 1))
     print(json.dumps(out))
 
 

@@ -43,6 +43,11 @@ WORKLOADS = {
     "quarter80x80x160_gr1e6": dict(nx=80, ny=80, nz=160, h=1 / 160, Gr=1e6, Pr=1.0,
                                    patch="none", bcs="quarter", design="quarter", seed=7,
                                    material=dict(alpha_max=1e5, q_alpha=8.0, q_f=0.881, Ck=1e-2)),
+    # the paper's larger mesh of the same quarter cavity (Sec. 6.4): 160 x 320 x 160
+    # elements, 41,603,205 unknowns (middle index vertical there, z here)
+    "quarter160x160x320_gr1e3": dict(nx=160, ny=160, nz=320, h=1 / 320, Gr=1e3, Pr=1.0,
+                                     patch="none", bcs="quarter", design="quarter", seed=7,
+                                     material=dict(alpha_max=1e5, q_alpha=8.0, q_f=0.881, Ck=1e-2)),
 }
 # Quarter-cavity geometry (fractions of the full unit cavity): heat-source block
 # 0.1 x 0.1 wide, 0.05 high at the centre of the bottom; design domain 0.75 x 0.75
