@@ -19,7 +19,8 @@ from oracle import solve as S  # noqa: E402
 from paper_1508_04596_gb300 import synth  # noqa: E402
 from tests.helpers import (oracle_problem, random_bc_state, sampled_rows,  # noqa: E402
                            sampled_stencil_rows, stencil_to_csr)
-from tests.test_gpu_parity import CASES, TOL32, TOL64, dev, host, make_pair, rel  # noqa: E402
+from tests.test_gpu_parity import (CASES, TOL32, TOL64, dev, host, make_pair,  # noqa: E402
+                                   quarter_pair, rel)
 
 
 @pytest.fixture(scope="module")
@@ -51,6 +52,20 @@ def test_assembled_matches_oracle_jacobian(nc, c):
     v = rng.standard_normal(prob.g.ndof)
     assert rel(host(gp.stencil_apply(S32, dev(v, torch.float32))), J @ v) <= TOL32
     assert rel(host(gp.stencil_apply(S32, dev(v, torch.float32), transpose=True)), J.T @ v) <= TOL32
+
+
+def test_assembled_quarter_cavity(nc):
+    """The paper's quarter cavity at 8 x 8 x 16 (symmetry planes, pinned pressure,
+    heat-source block, the paper's material parameters): the assembled stencil
+    equals the oracle's Jacobian, FP64 and FP32."""
+    prob, bc, gp, gam = quarter_pair(nc)
+    x = random_bc_state(prob, 35)
+    J = sp.csr_matrix(prob.jacobian(x, gam))
+    A = stencil_to_csr(host(gp.assemble(dev(x), dev(gam))), prob.g.nx, prob.g.ny, prob.g.nz)
+    assert spnorm(A - J) <= TOL64 * spnorm(J)
+    S32 = gp.assemble(dev(x, torch.float32), dev(gam, torch.float32))
+    v = np.random.default_rng(36).standard_normal(prob.g.ndof)
+    assert rel(host(gp.stencil_apply(S32, dev(v, torch.float32))), J @ v) <= TOL32
 
 
 def test_assembled_fins64_sampled_rows(nc):
