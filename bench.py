@@ -414,7 +414,8 @@ def assembled_operator(prob, x, gam, V, jvp_ms, jvp_lin_ms, stream, reps=5):
     against the matrix-free products (jvp_ms: nc_jvp; jvp_lin_ms: the benchmark
     step's time per product, linearisation store included).  Per node the product reads 675 FP64
     coefficients (5,400 B) and does 675 FMAs, so it is bound by the FP64 pipe
-    (1,350 flop per 5,480 B = 0.25 flop/B, above the 0.18 flop/B balance point)."""
+    (1,350 flop per 5,480 B = 0.25 flop/B, above the 0.18 flop/B balance point);
+    boundary nodes have fewer neighbours, and the counts below are exact."""
     import torch
     S = torch.empty(675 * prob.Nn, dtype=torch.float64, device=x.device)
     out = torch.empty_like(x)
@@ -436,8 +437,12 @@ def assembled_operator(prob, x, gam, V, jvp_ms, jvp_lin_ms, stream, reps=5):
     t_apply = a.elapsed_time(b) / NAPPLY
     ta = t_apply * 1e-3
     ref = jvp_lin_ms if jvp_lin_ms else jvp_ms
-    flops = 1350.0 * prob.Nn
-    nbytes = (5400.0 + 80.0) * prob.Nn
+    # (node, neighbour) pairs inside the grid: per axis 3 (n + 1) - 2
+    pairs = 1.0
+    for m in prob.level_dims(0):
+        pairs *= 3 * (m + 1) - 2
+    flops = 2.0 * 25 * pairs
+    nbytes = 8.0 * 25 * pairs + 80.0 * prob.Nn
     del S
     return {"build_ms": round(t_build, 3), "apply_ms": round(t_apply, 4),
             "gdofs": round(prob.ndof / ta / 1e9, 3),
