@@ -49,3 +49,22 @@ def test_default_opts(lib):
     from paper_1508_04596_gb300 import nc
     o = nc.default_opts()
     assert (o.rtol_newton, o.rtol_lin, o.restart, o.mixed) == (1e-8, 1e-5, 30, 1)
+    assert (o.galerkin, o.assembled) == (0, 0)
+
+
+@pytest.mark.parametrize("struct,fill,last", [("SolveOpts", "nc_default_opts", "assembled"),
+                                             ("MmaOpts", "nc_default_mma_opts", "df0_scale")])
+def test_option_structs_match_the_header(lib, struct, fill, last):
+    """The ctypes mirrors of the option structs have the C layout: the library's
+    default-filling call writes the mirror's last field and nothing beyond it."""
+    from paper_1508_04596_gb300 import nc
+    T = getattr(nc, struct)
+    n = ctypes.sizeof(T)
+    buf = (ctypes.c_ubyte * (n + 64))(*([0xA5] * (n + 64)))
+    o = T.from_buffer(buf)
+    getattr(nc.lib, fill)(ctypes.byref(o))
+    assert bytes(buf[n:]) == b"\xa5" * 64
+    ref = T()
+    getattr(nc.lib, fill)(ctypes.byref(ref))
+    assert getattr(o, last) == getattr(ref, last) and getattr(ref, last) != getattr(
+        T.from_buffer_copy(b"\xa5" * n), last)
