@@ -362,6 +362,20 @@ nc_status nc_level_dims(nc_ctx* ctx, int level, int* dims);
 nc_status nc_mg_apply(nc_ctx* ctx, int level, const double* x, const double* gamma, const void* v,
                       void* out, int prec, int transpose, int galerkin, void* stream);
 
+/* Grid sequencing (nested iteration for a cold start): transfers between level
+ * `level` (>= 1) of the hierarchy (nc_level_dims) and the finer level - 1.
+ * nc_coarsen_elem: e_coarse[E_level] = mean of the eight children in
+ * e_fine[E_{level-1}] (the design and source averaging of the hierarchy).
+ * nc_prolong_state: x_fine[5][Nn_{level-1}] = trilinear interpolation of
+ * x_coarse[5][Nn_level] (the multigrid prolongation), then the Dirichlet values
+ * of the finer grid imposed.  A problem set up on level l's grid with the same
+ * boundary conditions (and the pressure pin at node (i >> l, j >> l, k >> l))
+ * is the level-l problem of the hierarchy.  FP64 DEVICE arrays, async. */
+nc_status nc_coarsen_elem(nc_ctx* ctx, int level, const double* e_fine, double* e_coarse,
+                          void* stream);
+nc_status nc_prolong_state(nc_ctx* ctx, int level, const double* x_coarse, double* x_fine,
+                           void* stream);
+
 /* Adjoint solve J(x, gamma)^T lambda = rhs (Sec. 3.2) by FGMRES + multigrid on the
  * transposed operators, inside FP64 iterative refinement until
  * ||rhs - J^T lambda|| <= rtol_newton ||rhs||.  All FP64 [5][Nn].  Synchronous. */

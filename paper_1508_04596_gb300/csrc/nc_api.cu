@@ -411,6 +411,27 @@ nc_status nc_stencil_apply(nc_ctx* ctx, const void* S, const void* v, void* out,
   return cuda_check(ctx, cudaGetLastError(), "nc_stencil_apply");
 }
 
+nc_status nc_coarsen_elem(nc_ctx* ctx, int level, const double* e_fine, double* e_coarse,
+                          void* stream) {
+  if (!ctx || !e_fine || !e_coarse || level < 1 || level >= (int)ctx->lv.size())
+    return set_err(ctx, NC_ERR_ARG, "nc_coarsen_elem: bad argument");
+  op_coarsen_elem<double>(ctx->lv[level - 1].d, e_fine, ctx->lv[level].d, e_coarse,
+                          (cudaStream_t)stream);
+  return cuda_check(ctx, cudaGetLastError(), "nc_coarsen_elem");
+}
+
+nc_status nc_prolong_state(nc_ctx* ctx, int level, const double* x_coarse, double* x_fine,
+                           void* stream) {
+  if (!ctx || !x_coarse || !x_fine || level < 1 || level >= (int)ctx->lv.size())
+    return set_err(ctx, NC_ERR_ARG, "nc_prolong_state: bad argument");
+  const LevelDev& f = ctx->lv[level - 1].d;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaMemsetAsync(x_fine, 0, sizeof(double) * 5 * (size_t)f.Nn, s);
+  op_prolong_add<double>(ctx->lv[level].d, x_coarse, f, x_fine, s);
+  op_impose<double>(f, x_fine, s);
+  return cuda_check(ctx, cudaGetLastError(), "nc_prolong_state");
+}
+
 nc_status nc_objective(nc_ctx* ctx, const double* x, double* phi_host, double* dphidx,
                        void* stream) {
   if (!ctx || !x || !phi_host) return set_err(ctx, NC_ERR_ARG, "nc_objective: bad argument");

@@ -1,7 +1,7 @@
 """One design iteration of an optimisation run, for timing and profiling.
 
     python -m paper_1508_04596_gb300.design_iteration WORKLOAD [--fp64] [--no-adjoint] [--galerkin]
-                                                      [--assembled] [--restart M]
+                                                      [--assembled] [--restart M] [--sequence]
 
 Solves the state of the workload's design from a cold start, takes one
 synthetic optimiser step of the design (``synth.design_step``), then runs the
@@ -29,6 +29,8 @@ def main(argv=None):
     ap.add_argument("--assembled", action="store_true",
                     help="assemble every level's Jacobian into a block stencil")
     ap.add_argument("--restart", type=int, default=30, help="FGMRES restart (memory: 2 vectors each)")
+    ap.add_argument("--sequence", action="store_true",
+                    help="cold start by grid sequencing (solve the coarser grids first)")
     a = ap.parse_args(argv)
     mixed = 0 if a.fp64 else 1
     prob = nc.Problem.from_workload(a.workload, patch="flux")
@@ -39,10 +41,14 @@ def main(argv=None):
     x = torch.zeros(prob.ndof, dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    _, cinf = prob.newton_solve(g0, x, nc.default_opts(mixed=1, ramp_steps=3, restart=a.restart))
+    copts = nc.default_opts(mixed=1, ramp_steps=3, restart=a.restart)
+    if a.sequence:
+        _, cinf = prob.newton_solve_sequenced(g0, x, copts)
+    else:
+        _, cinf = prob.newton_solve(g0, x, copts)
     torch.cuda.synchronize()
     cold = {"cold_state_s": time.perf_counter() - t0, "cold_newton_its": cinf["newton_its"],
-            "cold_lin_its": cinf["lin_its_total"]}
+            "cold_lin_its": cinf["lin_its_total"], "cold_levels": cinf.get("levels")}
     # load the kernels and allocate the workspace of this precision (untimed)
     gal = 1 if a.galerkin else 0
     asm = 1 if a.assembled else 0

@@ -106,6 +106,8 @@ _SIGS = {
                                        ctypes.c_longlong, _vp, ctypes.POINTER(ctypes.c_double),
                                        ctypes.c_int, _vp]),
     "nc_level_dims": (ctypes.c_int, [_ctx, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "nc_coarsen_elem": (ctypes.c_int, [_ctx, ctypes.c_int, _vp, _vp, _vp]),
+    "nc_prolong_state": (ctypes.c_int, [_ctx, ctypes.c_int, _vp, _vp, _vp]),
     "nc_mg_apply": (ctypes.c_int, [_ctx, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_int, _vp]),
     "nc_volume": (ctypes.c_int, [_ctx, ctypes.c_longlong, _vp, _vp, ctypes.c_double,
@@ -195,6 +197,7 @@ class Problem:
 
     def __init__(self, params, bcs):
         self.params, self.bcs = params, bcs
+        self.source = None
         ctx = _ctx()
         st = lib.nc_setup(ctypes.byref(params), ctypes.byref(bcs), ctypes.byref(ctx))
         if st != 0:
@@ -328,6 +331,77 @@ class Problem:
                                   self._prec(v), int(transpose), int(galerkin), _stream(stream)))
         return out
 
+    # ---- grid sequencing ----------------------------------------------------
+    def coarse_problem(self):
+        """The problem on the next coarser grid of the multigrid hierarchy (element
+        counts halved, h doubled, the same boundary conditions, the pressure pin
+        at the coarse node (i >> 1, j >> 1, k >> 1), the element source averaged
+        over the children), or None when the grid does not halve."""
+        d = (ctypes.c_int * 3)()
+        if lib.nc_level_dims(self.ctx, 1, d) != 0:
+            return None
+        p = Params.from_buffer_copy(self.params)
+        p.nx, p.ny, p.nz, p.h = d[0], d[1], d[2], 2.0 * self.params.h
+        b = BCs.from_buffer_copy(self.bcs)
+        if b.p_pin >= 0:
+            nx1, ny1 = self.params.nx + 1, self.params.ny + 1
+            i, j, k = b.p_pin % nx1, (b.p_pin // nx1) % ny1, b.p_pin // (nx1 * ny1)
+            b.p_pin = (i >> 1) + (d[0] + 1) * ((j >> 1) + (d[1] + 1) * (k >> 1))
+        c = Problem(p, b)
+        if self.source is not None:
+            c.set_source(self.coarsen(self.source))
+        return c
+
+    def coarsen(self, e, stream=None):
+        """Element field on the next coarser grid: the mean of each element's 8 children."""
+        d = (ctypes.c_int * 3)()
+        self._chk(lib.nc_level_dims(self.ctx, 1, d))
+        out = torch.empty(d[0] * d[1] * d[2], dtype=torch.float64, device=e.device)
+        self._chk(lib.nc_coarsen_elem(self.ctx, 1, self._vec(e, torch.float64, self.E, "e"),
+                                      ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def prolong(self, xc, stream=None):
+        """State on this grid from the next coarser grid's (trilinear, Dirichlet
+        values imposed)."""
+        d = (ctypes.c_int * 3)()
+        self._chk(lib.nc_level_dims(self.ctx, 1, d))
+        nc_ = 5 * (d[0] + 1) * (d[1] + 1) * (d[2] + 1)
+        out = torch.empty(self.ndof, dtype=torch.float64, device=xc.device)
+        self._chk(lib.nc_prolong_state(self.ctx, 1, self._vec(xc, torch.float64, nc_, "x_coarse"),
+                                       ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def newton_solve_sequenced(self, gam, x, opts=None, coarse_opts=None, stream=None, check=True):
+        """Cold start by grid sequencing (nested iteration): the state is solved on
+        every coarser grid of the hierarchy first, coarsest first, and each
+        solution, prolonged, starts the solve on the next finer grid; x receives
+        the solution on this grid.  coarse_opts (default opts) apply to the
+        coarser solves.  Returns (x, info) of the final solve, with
+        info["levels"] reporting the coarser ones (coarsest first)."""
+        chain, gams = [self], [gam]
+        while True:
+            c = chain[-1].coarse_problem()
+            if c is None:
+                break
+            gams.append(chain[-1].coarsen(gams[-1], stream))
+            chain.append(c)
+        xs = torch.zeros(chain[-1].ndof, dtype=torch.float64, device=x.device)
+        levels = []
+        for k in range(len(chain) - 1, 0, -1):
+            _, inf = chain[k].newton_solve(gams[k], xs, coarse_opts or opts, stream, check=False)
+            pk = chain[k].params
+            levels.append(dict(dims=(pk.nx, pk.ny, pk.nz), status=inf["status"],
+                               newton_its=inf["newton_its"], lin_its=inf["lin_its_total"],
+                               seconds=inf["seconds"]))
+            xs = chain[k - 1].prolong(xs, stream)
+            chain[k].close()  # free the coarser context before the finer solve
+        x.copy_(xs)
+        del xs
+        _, info = self.newton_solve(gam, x, opts, stream, check)
+        info["levels"] = levels
+        return x, info
+
     # ---- design update (Sec. 3.2) ------------------------------------------
     def volume(self, gam, active=None, vf=0.05, grad=None, stream=None):
         """Normalised volume constraint g = sum_active (1 - gamma)/(vf n_active) - 1
@@ -422,6 +496,7 @@ class Problem:
     def set_source(self, s_e, stream=None):
         p = None if s_e is None else self._vec(s_e, torch.float64, self.E, "source")
         self._chk(lib.nc_set_source(self.ctx, p, _stream(stream)))
+        self.source = s_e
 
     def objective(self, x, want_grad=True, stream=None):
         phi = ctypes.c_double()

@@ -223,3 +223,38 @@ def test_optimisation_checkpoint_resume(nc, tmp_path):
     assert [r["phi"] for r in hb] == [r["phi"] for r in ha[2:]]
     for k in ("rho", "xold1", "xold2", "low", "upp", "x"):
         assert torch.equal(getattr(a, k), getattr(b, k)), k
+
+
+def test_grid_sequencing_cold_start(nc):
+    """Nested iteration (grid sequencing): on the 12^3 cavity (grids 3^3, 6^3,
+    12^3) the sequenced cold start reaches the oracle's Newton solution; on the
+    16 x 16 x 32 quarter cavity (pressure pin and heat source carried to the
+    coarser grids) it reaches the plain cold start's solution with no more
+    fine-grid FGMRES iterations."""
+    from oracle import solve as S
+    from tests.helpers import oracle_problem
+    name = "cavity12_gr1e3"
+    cfg = synth.WORKLOADS[name]
+    prob, _ = oracle_problem(12, 12, 12, cfg["h"], cfg["Gr"], cfg["Pr"])
+    gam = synth.design(name)
+    xo, _ = S.newton(prob, gam, np.zeros((5, prob.g.Nn)), rtol=1e-12)
+    gp = nc.Problem.from_workload(name)
+    x = torch.zeros(gp.ndof, dtype=torch.float64, device="cuda")
+    _, info = gp.newton_solve_sequenced(dev(gam), x, nc.default_opts(rtol_newton=1e-10))
+    assert info["status"] == "NC_OK" and [lv["dims"] for lv in info["levels"]] == [(3, 3, 3), (6, 6, 6)]
+    assert all(lv["status"] == "NC_OK" for lv in info["levels"]), info["levels"]
+    assert float(np.linalg.norm(x.cpu().numpy() - xo.ravel()) / np.linalg.norm(xo)) <= 1e-8
+
+    kw = dict(nx=16, ny=16, nz=32, h=1.0 / 32)
+    qname = "quarter80x80x160_gr1e3"
+    gq = dev(synth.design(dict(synth.WORKLOADS[qname], **kw)))
+    opts = nc.default_opts(rtol_newton=1e-10)
+    qa = nc.Problem.from_workload(qname, **kw)
+    xa = torch.zeros(qa.ndof, dtype=torch.float64, device="cuda")
+    _, ia = qa.newton_solve(gq, xa, opts)
+    qb = nc.Problem.from_workload(qname, **kw)
+    xb = torch.zeros(qb.ndof, dtype=torch.float64, device="cuda")
+    _, ib = qb.newton_solve_sequenced(gq, xb, opts)
+    assert ib["status"] == "NC_OK" and len(ib["levels"]) >= 2
+    assert float(torch.linalg.norm(xa - xb) / torch.linalg.norm(xa)) <= 1e-8
+    assert ib["lin_its_total"] <= ia["lin_its_total"], (ia, ib)
