@@ -43,9 +43,13 @@ WORKLOADS = {
     "quarter80x80x160_gr1e6": dict(nx=80, ny=80, nz=160, h=1 / 160, Gr=1e6, Pr=1.0,
                                    patch="none", bcs="quarter", design="quarter", seed=7,
                                    material=dict(alpha_max=1e5, q_alpha=8.0, q_f=0.881, Ck=1e-2)),
-    # the paper's larger mesh of the same quarter cavity (Sec. 6.4): 160 x 320 x 160
-    # elements, 41,603,205 unknowns (middle index vertical there, z here)
+    # the paper's larger meshes of the same quarter cavity (Sec. 6.4): 160 x 320 x 160
+    # elements, 41,603,205 unknowns, and 320 x 640 x 320 elements, 330,246,405
+    # unknowns (middle index vertical there, z here)
     "quarter160x160x320_gr1e3": dict(nx=160, ny=160, nz=320, h=1 / 320, Gr=1e3, Pr=1.0,
+                                     patch="none", bcs="quarter", design="quarter", seed=7,
+                                     material=dict(alpha_max=1e5, q_alpha=8.0, q_f=0.881, Ck=1e-2)),
+    "quarter320x320x640_gr1e3": dict(nx=320, ny=320, nz=640, h=1 / 640, Gr=1e3, Pr=1.0,
                                      patch="none", bcs="quarter", design="quarter", seed=7,
                                      material=dict(alpha_max=1e5, q_alpha=8.0, q_f=0.881, Ck=1e-2)),
 }
