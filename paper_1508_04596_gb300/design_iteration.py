@@ -48,7 +48,8 @@ def main(argv=None):
         _, cinf = prob.newton_solve(g0, x, copts)
     torch.cuda.synchronize()
     cold = {"cold_state_s": time.perf_counter() - t0, "cold_newton_its": cinf["newton_its"],
-            "cold_lin_its": cinf["lin_its_total"], "cold_levels": cinf.get("levels")}
+            "cold_lin_its": cinf["lin_its_total"], "cold_levels": cinf.get("levels"),
+            "cold_res_hist": cinf["res_hist"]}
     # load the kernels and allocate the workspace of this precision (untimed)
     gal = 1 if a.galerkin else 0
     asm = 1 if a.assembled else 0
@@ -67,7 +68,8 @@ def main(argv=None):
     torch.cuda.synchronize()
     out = {"workload": a.workload, "mixed": mixed, "galerkin": gal, "assembled": asm,
            "state_s": time.perf_counter() - t0, "newton_its": inf["newton_its"],
-           "lin_its": inf["lin_its_total"], "state_status": inf["status"]}
+           "lin_its": inf["lin_its_total"], "state_status": inf["status"],
+           "state_res_hist": inf["res_hist"]}
     if not a.no_adjoint:
         t0 = time.perf_counter()
         phi, dphi = prob.objective(x)
