@@ -1,6 +1,9 @@
-"""Host build of the CUDA path's element header: the specialised element
-columns of the assembled Jacobian equal the general element products
-(tests/host/element_columns_check.cpp), without a GPU."""
+"""Host builds of the CUDA path's element header (plain C++ outside nvcc),
+without a GPU: the element tangent against central differences of the element
+residual, its transpose, diagonal, linearisation-store and design-sensitivity
+variants against it (tests/host/element_consistency_check.cpp), and the
+specialised element columns of the assembled Jacobian against the general
+products (tests/host/element_columns_check.cpp)."""
 import os
 import shutil
 import subprocess
@@ -10,13 +13,13 @@ import pytest
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-def test_element_columns_match_general_products(tmp_path):
+@pytest.mark.parametrize("prog", ["element_consistency_check", "element_columns_check"])
+def test_element_routines_on_the_host(tmp_path, prog):
     cxx = shutil.which("g++") or shutil.which("c++")
     if cxx is None:
         pytest.skip("no C++ compiler")
-    exe = str(tmp_path / "element_columns_check")
-    subprocess.run([cxx, "-std=c++17", "-O1", os.path.join(HERE, "host", "element_columns_check.cpp"),
-                    "-o", exe], check=True)
+    exe = str(tmp_path / prog)
+    subprocess.run([cxx, "-std=c++17", "-O1", os.path.join(HERE, "host", prog + ".cpp"), "-o", exe],
+                   check=True)
     r = subprocess.run([exe], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
-    assert float(r.stdout.strip()) <= 1e-12
