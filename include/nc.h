@@ -225,7 +225,9 @@ nc_status nc_filter(nc_ctx* ctx, const double* rho, double* gamma_f, double radi
 
 /* Solver options.  rtol_newton: stop when ||R|| <= max(rtol_newton ||R_0||,
  * atol_newton) (Sec. 5.1 uses a relative tolerance);
- * rtol_lin: FGMRES relative tolerance per linear solve (Sec. 5.2); max_newton,
+ * rtol_lin: FGMRES relative tolerance per linear solve (Sec. 5.2), loosened inside
+ * Newton to 0.01 of the Newton target divided by the current ||R|| when that is
+ * larger (the last step near the target); max_newton,
  * max_lin (total FGMRES iterations per linear solve), restart (FGMRES restart,
  * <= 64); mg_levels: multigrid levels to use (0 = all); smooth_its: Jacobi-GMRES
  * smoothing iterations per pre/post step; coarse_its: Jacobi-GMRES iterations on
