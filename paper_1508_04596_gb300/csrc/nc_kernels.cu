@@ -85,8 +85,11 @@ __global__ void __launch_bounds__(ELEM_THREADS) k_elem_res(LevelDev d, ElemConst
   store_elem(d.E, e, out, Y);
 }
 
+// Three blocks per SM (at most 168 registers, a few spilled): 12 warps per SM hide
+// more latency than 8 at 255 registers; measured 9.6 % faster in FP32 and
+// unchanged in FP64.
 template <typename R, bool TRANSPOSE>
-__global__ void __launch_bounds__(ELEM_THREADS) k_elem_lin(LevelDev d, ElemConst<R> c,
+__global__ void __launch_bounds__(ELEM_THREADS, 3) k_elem_lin(LevelDev d, ElemConst<R> c,
                                                            const R* __restrict__ x,
                                                            const R* __restrict__ gam,
                                                            const R* __restrict__ src,
