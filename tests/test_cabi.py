@@ -68,3 +68,25 @@ def test_option_structs_match_the_header(lib, struct, fill, last):
     getattr(nc.lib, fill)(ctypes.byref(ref))
     assert getattr(o, last) == getattr(ref, last) and getattr(ref, last) != getattr(
         T.from_buffer_copy(b"\xa5" * n), last)
+
+
+def test_quarter_workloads_have_the_papers_sizes(lib):
+    """The quarter-cavity workloads are the paper's three meshes (Sec. 6.2-6.4,
+    tests/golden/paper_dof_counts.txt, the paper's middle index vertical there
+    and z here): nc_sizes gives the printed DOF and element counts."""
+    from paper_1508_04596_gb300 import nc, synth
+    path = os.path.join(ROOT, "tests", "golden", "paper_dof_counts.txt")
+    printed = {(int(r[0]), int(r[2]), int(r[1])): (int(r[3]), int(r[4]))
+               for r in (l.split() for l in open(path) if l.strip() and not l.startswith("#"))}
+    seen = set()
+    for name, cfg in synth.WORKLOADS.items():
+        if cfg.get("bcs") != "quarter":
+            continue
+        key = (cfg["nx"], cfg["ny"], cfg["nz"])
+        p = nc.make_params(*key, cfg["h"], cfg["Gr"], cfg["Pr"])
+        nn, ne, nd = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        assert nc.lib.nc_sizes(ctypes.byref(p), ctypes.byref(nn), ctypes.byref(ne), ctypes.byref(nd)) == 0
+        assert (nd.value, ne.value) == printed[key], name
+        assert cfg["h"] * cfg["nz"] == pytest.approx(1.0)  # unit cavity height
+        seen.add(key)
+    assert len(seen) == 3
