@@ -186,6 +186,17 @@ def mv_ld(n):
     return (n + 63) // 64 * 64
 
 
+def coarse_pin(pin, fine_xy, coarse_xy):
+    """Node index of a pressure pin on the next coarser grid: fine node (i, j, k)
+    -> coarse node (i >> 1, j >> 1, k >> 1), as the multigrid hierarchy places it
+    (-1, no pin, stays -1).  fine_xy / coarse_xy: element counts (nx, ny)."""
+    if pin < 0:
+        return pin
+    nx1, ny1 = fine_xy[0] + 1, fine_xy[1] + 1
+    i, j, k = pin % nx1, (pin // nx1) % ny1, pin // (nx1 * ny1)
+    return (i >> 1) + (coarse_xy[0] + 1) * ((j >> 1) + (coarse_xy[1] + 1) * (k >> 1))
+
+
 def _stream(stream):
     if stream is None:
         return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -343,10 +354,7 @@ class Problem:
         p = Params.from_buffer_copy(self.params)
         p.nx, p.ny, p.nz, p.h = d[0], d[1], d[2], 2.0 * self.params.h
         b = BCs.from_buffer_copy(self.bcs)
-        if b.p_pin >= 0:
-            nx1, ny1 = self.params.nx + 1, self.params.ny + 1
-            i, j, k = b.p_pin % nx1, (b.p_pin // nx1) % ny1, b.p_pin // (nx1 * ny1)
-            b.p_pin = (i >> 1) + (d[0] + 1) * ((j >> 1) + (d[1] + 1) * (k >> 1))
+        b.p_pin = coarse_pin(b.p_pin, (self.params.nx, self.params.ny), (d[0], d[1]))
         c = Problem(p, b)
         if self.source is not None:
             c.set_source(self.coarsen(self.source))
