@@ -65,7 +65,10 @@ typedef struct {
   double g_dir[3];    /* unit gravity direction e^g, e.g. (0,0,-1) */
 } nc_params;
 
-/* Boundary conditions per face, order (-x, +x, -y, +y, -z, +z).
+/* Boundary conditions of the cavity problems (Sec. 6.1: cold vertical and top
+ * walls, insulated bottom, symmetry planes of the quarter domain, closed walls;
+ * the benchmark cavities heat a patch of the bottom instead of a source block).
+ * Per face, order (-x, +x, -y, +y, -z, +z).
  * Velocity: NC_VEL_NOSLIP (u = 0), NC_VEL_FREE (traction-free, natural),
  * NC_VEL_SYMMETRY (normal component 0).  Temperature: NC_T_ADIABATIC or
  * NC_T_DIRICHLET with value T_val[face].  A rectangular patch of the bottom face,
@@ -86,14 +89,23 @@ typedef struct {
   long long p_pin;
 } nc_bcs;
 
-/* Sizes of the discrete problem, computed without allocating anything.
+/* Sizes of the discrete problem (Sec. 4: trilinear hexahedra on a structured
+ * grid, 5 unknowns per node; Sec. 6.2-6.4 quote the resulting unknown counts,
+ * e.g. 5,281,605 for 80 x 160 x 80 elements): n_nodes = (nx+1)(ny+1)(nz+1),
+ * n_elems = nx ny nz, n_dof = 5 n_nodes, computed without allocating anything.
  * Any output pointer may be NULL.  Returns NC_ERR_ARG for invalid sizes. */
 nc_status nc_sizes(const nc_params* prm, long long* n_nodes, long long* n_elems,
                    long long* n_dof);
 
-/* Create a context on the current CUDA device: boundary-condition flags, the
- * multigrid level hierarchy (halving while every dimension stays even and at
- * least 2 elements remain) and all operator workspace are allocated here.
+/* Create a context on the current CUDA device for the discretised problem of
+ * Sec. 2 and Sec. 4 with the boundary conditions of Sec. 6.1 (bcs) and the
+ * material interpolation of Sec. 3.1 (prm): boundary-condition flags, the
+ * geometric multigrid hierarchy of Sec. 5.2 (halving while every dimension stays
+ * even and at least 2 elements remain) and all operator workspace are allocated
+ * here.  prm and bcs are copied; the caller keeps ownership of both.
+ * NC_ERR_ARG for invalid parameters (non-positive sizes, h, Pr or Ck, a face
+ * condition or patch mode out of range, a pinned node outside the grid),
+ * NC_ERR_OOM if an allocation fails.
  * Krylov workspace is allocated at the first solve (sized by its restart).
  * On failure *out is NULL and the status says why. */
 nc_status nc_setup(const nc_params* prm, const nc_bcs* bcs, nc_ctx** out);
@@ -117,7 +129,11 @@ nc_status nc_bc_flags(nc_ctx* ctx, unsigned char* flags_host);
  * Synchronous with respect to the given stream. */
 nc_status nc_set_source(nc_ctx* ctx, const double* source_e, void* stream);
 
-/* x_inout[D] := x_D (the Dirichlet values of the boundary conditions). */
+/* x_inout[D] := x_D: the Dirichlet values of the boundary conditions (Sec. 6.1:
+ * zero velocity on walls, zero normal velocity on symmetry planes, T = 0 on the
+ * cold walls, the prescribed patch temperature, p = 0 at a pinned node); other
+ * entries are left unchanged.  x_inout: [5][Nn] DEVICE, double (NC_FP64) or
+ * float (NC_FP32), owned by the caller.  Asynchronous on stream. */
 nc_status nc_impose_dirichlet(nc_ctx* ctx, void* x_inout, int prec, void* stream);
 
 /* Residual R(x, gamma) of the stabilised weak form (Sec. 4; App. B) plus the
@@ -206,10 +222,22 @@ nc_status nc_sensitivity(nc_ctx* ctx, const double* x, const double* gamma,
  * keeps the last call's contents; nothing in it needs to start at zero.  All
  * calls share it, so calls whose work can overlap on the GPU (different streams
  * or threads without ordering) race and must be serialised by the caller.
- * Errors: NC_ERR_ARG (NULL pointer, bad sizes or ids), NC_ERR_SIZE, NC_ERR_CUDA. */
+ * Errors: NC_ERR_ARG (a NULL pointer, or parameters or boundary conditions that
+ * nc_setup would reject: sizes, coefficients, face conditions, patch mode, pinned
+ * node), NC_ERR_SIZE, NC_ERR_CUDA. */
 #define NC_STATIC_SCRATCH_BYTES (64ull << 20)
 nc_status nc_jvp_static(const nc_params* prm, const nc_bcs* bcs, const void* x,
                         const void* gamma, const void* v, void* Jv, int prec, void* stream);
+
+/* ALU throughput probe (a measurement helper; the paper has no counterpart).
+ * The element operators are bound by the FP32 / FP64 pipes, so their roofline
+ * is an arithmetic peak; this call measures what dependent FMA chains reach:
+ * `blocks` blocks of 256 threads, each thread 8 independent chains of `iters`
+ * fused multiply-adds (iters a positive multiple of 16), in double (NC_FP64) or
+ * float (NC_FP32).  That is 16 * iters * blocks * 256 flop; time it with events
+ * on `stream`.  out: DEVICE, blocks * 256 values of the precision, receives each
+ * thread's chain sum.  Asynchronous.  NC_ERR_ARG for invalid arguments. */
+nc_status nc_fma_probe(int prec, int blocks, long long iters, void* out, void* stream);
 
 /* PDE (Helmholtz) density filter (Sec. 3.2; [Lazarov & Sigmund 2011]; the paper
  * uses radius = 2.5 h, Sec. 6.3-6.4): solves -r^2 lap(rho~) + rho~ = rho with
@@ -254,6 +282,11 @@ typedef struct {
                           and applied as such; pays off in FP64 (mixed = 0), where an assembled
                           product costs about 0.4 of a matrix-free one and the assembly about
                           20 products; 0 (default): matrix-free */
+  double rtol_adjoint; /* nc_adjoint_solve stops when ||rhs - J^T lambda|| <= rtol_adjoint ||rhs||
+                          (default 1e-10; nc_newton_solve ignores it).  A residual bounds the
+                          solution error only through the conditioning of J, so the adjoint
+                          is solved 100 times tighter than the state's default 1e-8: the
+                          mixed and FP64 sensitivities then agree to about 1e-9 */
 } nc_solve_opts;
 
 /* Per-solve report (Sec. 6.2 reports Newton and linear iteration counts). */
@@ -265,7 +298,7 @@ typedef struct {
 
 /* Fill opts with defaults (rtol_newton 1e-8, rtol_lin 1e-5, max_newton 30,
  * max_lin 200, restart 30, all levels, smooth_its 6, coarse_its 30, mixed 1,
- * ramp_steps 0, atol_newton 0, galerkin 0, assembled 0). */
+ * ramp_steps 0, atol_newton 0, galerkin 0, assembled 0, rtol_adjoint 1e-10). */
 void nc_default_opts(nc_solve_opts* opts);
 
 /* Damped Newton (Sec. 5.1) on R(x, gamma) = 0 from x_inout (Dirichlet values
@@ -380,7 +413,8 @@ nc_status nc_prolong_state(nc_ctx* ctx, int level, const double* x_coarse, doubl
 
 /* Adjoint solve J(x, gamma)^T lambda = rhs (Sec. 3.2) by FGMRES + multigrid on the
  * transposed operators, inside FP64 iterative refinement until
- * ||rhs - J^T lambda|| <= rtol_newton ||rhs||.  All FP64 [5][Nn].  Synchronous. */
+ * ||rhs - J^T lambda|| <= rtol_adjoint ||rhs|| (max_newton refinement sweeps at
+ * most).  All FP64 [5][Nn].  Synchronous. */
 nc_status nc_adjoint_solve(nc_ctx* ctx, const double* x, const double* gamma,
                            const double* rhs, double* lambda_out, const nc_solve_opts* opts,
                            nc_solve_info* info, void* stream);

@@ -22,20 +22,46 @@ nc_status cuda_check(nc_ctx* ctx, cudaError_t e, const char* what) {
 }
 }  // namespace nc
 
-namespace {
+namespace nc {
 
 bool valid_params(const nc_params* p, std::string& why) {
   if (!p) { why = "params is NULL"; return false; }
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) { why = "nx, ny, nz must be >= 1"; return false; }
+  // bounded first, so that no product of the sizes below can overflow
+  if (p->nx > MAX_DIM || p->ny > MAX_DIM || p->nz > MAX_DIM) {
+    why = "nx, ny, nz must be <= 2^20";
+    return false;
+  }
   if (!(p->h > 0.0) || !std::isfinite(p->h)) { why = "h must be positive and finite"; return false; }
   const long long Nn = (long long)(p->nx + 1) * (p->ny + 1) * (p->nz + 1);
   if (Nn > (1LL << 40)) { why = "grid too large"; return false; }
-  if (!(p->Pr > 0.0)) { why = "Pr must be positive"; return false; }
-  if (!(p->Ck > 0.0)) { why = "Ck must be positive"; return false; }
-  if (!(p->alpha_max >= 0.0)) { why = "alpha_max must be >= 0"; return false; }
+  if (!(p->Pr > 0.0) || !std::isfinite(p->Pr)) { why = "Pr must be positive and finite"; return false; }
+  if (!(p->Ck > 0.0) || !std::isfinite(p->Ck)) { why = "Ck must be positive and finite"; return false; }
+  if (!(p->alpha_max >= 0.0) || !std::isfinite(p->alpha_max)) {
+    why = "alpha_max must be >= 0 and finite";
+    return false;
+  }
   if (!std::isfinite(p->Gr)) { why = "Gr must be finite"; return false; }
   return true;
 }
+
+bool valid_bcs(const nc_params& p, const nc_bcs* b, std::string& why) {
+  if (!b) { why = "bcs is NULL"; return false; }
+  for (int f = 0; f < 6; ++f) {
+    if (b->vel_bc[f] < 0 || b->vel_bc[f] > 2) { why = "vel_bc out of range"; return false; }
+    if (b->T_bc[f] < 0 || b->T_bc[f] > 1) { why = "T_bc out of range"; return false; }
+  }
+  if (b->patch_mode < 0 || b->patch_mode > 2) { why = "patch_mode out of range"; return false; }
+  if (b->p_pin >= (long long)(p.nx + 1) * (p.ny + 1) * (p.nz + 1)) {
+    why = "p_pin outside the grid";
+    return false;
+  }
+  return true;
+}
+
+}  // namespace nc
+
+namespace {
 
 // Boundary flags of one level: bits 0..4 Dirichlet per field, bits 5..7 index
 // of the Dirichlet temperature value.  Precedence of temperature values:
@@ -183,12 +209,7 @@ nc_status nc_setup(const nc_params* prm, const nc_bcs* bcs, nc_ctx** out) {
   if (!out) return NC_ERR_ARG;
   *out = nullptr;
   std::string why;
-  if (!valid_params(prm, why) || !bcs) return NC_ERR_ARG;
-  for (int f = 0; f < 6; ++f) {
-    if (bcs->vel_bc[f] < 0 || bcs->vel_bc[f] > 2) return NC_ERR_ARG;
-    if (bcs->T_bc[f] < 0 || bcs->T_bc[f] > 1) return NC_ERR_ARG;
-  }
-  if (bcs->patch_mode < 0 || bcs->patch_mode > 2) return NC_ERR_ARG;
+  if (!valid_params(prm, why) || !valid_bcs(*prm, bcs, why)) return NC_ERR_ARG;
   nc_ctx* ctx = new (std::nothrow) nc_ctx();
   if (!ctx) return NC_ERR_OOM;
   ctx->prm = *prm;
@@ -201,7 +222,6 @@ nc_status nc_setup(const nc_params* prm, const nc_bcs* bcs, nc_ctx** out) {
   // coarse node (pi >> l, pj >> l, pk >> l)
   long long pin_ijk[3] = {-1, -1, -1};
   if (bcs->p_pin >= 0) {
-    if (bcs->p_pin >= (long long)(nx + 1) * (ny + 1) * (nz + 1)) { delete ctx; return NC_ERR_ARG; }
     pin_ijk[0] = bcs->p_pin % (nx + 1);
     pin_ijk[1] = (bcs->p_pin / (nx + 1)) % (ny + 1);
     pin_ijk[2] = bcs->p_pin / ((long long)(nx + 1) * (ny + 1));

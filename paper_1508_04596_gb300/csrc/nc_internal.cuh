@@ -16,6 +16,14 @@ constexpr int MAX_LEVELS = 16;
 constexpr int RED_THREADS = 256;
 constexpr int RED_BLOCKS_MAX = 608;  // 4 x 152 SMs
 constexpr int MAX_RESTART = 64;
+constexpr int MAX_DIM = 1 << 20;  // largest element count per direction
+
+// Argument checks shared by nc_setup and nc_jvp_static (nc_api.cu): finite
+// positive sizes and coefficients, every dimension <= MAX_DIM (checked before
+// any product of them is formed), face conditions and the patch mode in range,
+// the pinned node inside the grid.  why receives the reason of a rejection.
+bool valid_params(const nc_params* p, std::string& why);
+bool valid_bcs(const nc_params& p, const nc_bcs* b, std::string& why);
 
 // Geometry and boundary data of one grid level, passed to kernels by value.
 struct LevelDev {

@@ -524,7 +524,7 @@ nc_status prepare(nc_ctx* ctx, const nc_solve_opts& o, int nlev, bool mixed) {
   if (o.restart < 1 || o.restart > MAX_RESTART || o.smooth_its < 1 ||
       o.smooth_its > MAX_RESTART || o.coarse_its < 1 || o.coarse_its > MAX_RESTART ||
       o.max_lin < 1 || o.max_newton < 0 || !(o.rtol_lin > 0.0) || !(o.rtol_newton >= 0.0) ||
-      !(o.atol_newton >= 0.0))
+      !(o.atol_newton >= 0.0) || !(o.rtol_adjoint >= 0.0))
     return set_err(ctx, NC_ERR_ARG, "invalid solver options");
   if (ctx->kry.m < o.restart) {
     cudaFree(ctx->kry.V);
@@ -679,6 +679,7 @@ void nc_default_opts(nc_solve_opts* o) {
   o->atol_newton = 0.0;
   o->galerkin = 0;
   o->assembled = 0;
+  o->rtol_adjoint = 1e-10;
 }
 
 nc_status nc_newton_solve(nc_ctx* ctx, const double* gam, double* x, const nc_solve_opts* opts,
@@ -851,7 +852,7 @@ nc_status nc_adjoint_solve(nc_ctx* ctx, const double* x, const double* gam, cons
     // the state and the design do not change during the refinement: one
     // linearisation of every level serves all sweeps
     bool linearized = false;
-    while (st == NC_OK && nr > o.rtol_newton * nb && nr > 0.0) {
+    while (st == NC_OK && nr > o.rtol_adjoint * nb && nr > 0.0) {
       if (k >= o.max_newton) { st = set_err(ctx, NC_ERR_MAXIT, "adjoint refinement limit"); break; }
       if (!linearized) {
         st = mixed ? linearize<float>(ctx, nlev, x, gam, s, o)
@@ -861,7 +862,7 @@ nc_status nc_adjoint_solve(nc_ctx* ctx, const double* x, const double* gam, cons
       }
       int lits = 0;
       // inner relative tolerance: no tighter than needed for the outer target
-      const double rt = std::fmax(o.rtol_lin, 0.5 * o.rtol_newton * nb / nr);
+      const double rt = std::fmax(o.rtol_lin, 0.5 * o.rtol_adjoint * nb / nr);
       st = fgmres(ctx, ls, o, r, dl, std::fmin(rt, 0.5), &lits, s);
       info.lin_its_total += lits;
       if (st != NC_OK && st != NC_ERR_MAXIT) break;

@@ -113,17 +113,14 @@ extern "C" nc_status nc_jvp_static(const nc_params* prm, const nc_bcs* bcs, cons
                                    void* stream) {
   if (!prm || !bcs || !x || !gamma || !v || !Jv || (prec != NC_FP64 && prec != NC_FP32))
     return NC_ERR_ARG;
-  if (prm->nx < 1 || prm->ny < 1 || prm->nz < 1 || !(prm->h > 0.0) || !(prm->Pr > 0.0) ||
-      !(prm->Ck > 0.0))
-    return NC_ERR_ARG;
-  for (int f = 0; f < 6; ++f)
-    if (bcs->vel_bc[f] < 0 || bcs->vel_bc[f] > 2 || bcs->T_bc[f] < 0 || bcs->T_bc[f] > 1)
-      return NC_ERR_ARG;
+  // the checks of nc_setup: sizes bounded before any product of them is formed,
+  // finite coefficients, face conditions, patch mode and pinned node in range
+  std::string why;
+  if (!valid_params(prm, why) || !valid_bcs(*prm, bcs, why)) return NC_ERR_ARG;
   LevelDev d;
   d.nx = prm->nx; d.ny = prm->ny; d.nz = prm->nz; d.h = prm->h;
   d.Nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
   d.E = (long long)d.nx * d.ny * d.nz;
-  if (bcs->p_pin >= d.Nn) return NC_ERR_ARG;
   // scratch: flags (Nn bytes, rounded up to 256), then 40 rows per element
   const size_t esz = prec == NC_FP64 ? sizeof(double) : sizeof(float);
   const size_t flag_bytes = ((size_t)d.Nn + 255) / 256 * 256;

@@ -11,7 +11,7 @@ import os
 
 import torch
 
-from . import synth
+from . import cavity, synth
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libnc.so")
@@ -51,7 +51,7 @@ class SolveOpts(ctypes.Structure):
                 ("smooth_its", ctypes.c_int), ("coarse_its", ctypes.c_int),
                 ("mixed", ctypes.c_int), ("ramp_steps", ctypes.c_int),
                 ("atol_newton", ctypes.c_double), ("galerkin", ctypes.c_int),
-                ("assembled", ctypes.c_int)]
+                ("assembled", ctypes.c_int), ("rtol_adjoint", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -227,7 +227,8 @@ class Problem:
         p = make_params(cfg["nx"], cfg["ny"], cfg["nz"], cfg["h"], cfg["Gr"], cfg["Pr"], **mat)
         if cfg.get("bcs") == "quarter":
             prob = cls(p, quarter_bcs(cfg["nx"], cfg["ny"], cfg["nz"]))
-            prob.set_source(torch.tensor(synth.source(cfg), dtype=torch.float64, device="cuda"))
+            s_e = cavity.source(cfg["nx"], cfg["ny"], cfg["nz"], cfg["h"], True)
+            prob.set_source(torch.tensor(s_e, dtype=torch.float64, device="cuda"))
             return prob
         mode = PATCH_FLUX if cfg["patch"] == "flux" else PATCH_DIRICHLET
         return cls(p, cavity_bcs(mode, 1.0))

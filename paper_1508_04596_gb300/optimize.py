@@ -35,7 +35,7 @@ import time
 import numpy as np
 import torch
 
-from . import nc, synth
+from . import cavity, nc, synth
 
 CONTINUATION = [dict(q_f=0.881, q_alpha=8.0, alpha_max=1e5),
                 dict(q_f=8.81, q_alpha=8.0, alpha_max=1e5),
@@ -46,14 +46,8 @@ CONTINUATION = [dict(q_f=0.881, q_alpha=8.0, alpha_max=1e5),
 
 def regions(cfg):
     """(active design elements, fixed values of the passive elements)."""
-    nx, ny, nz, h = cfg["nx"], cfg["ny"], cfg["nz"], cfg["h"]
-    if cfg.get("bcs") == "quarter":
-        src, des = synth.quarter_regions(nx, ny, nz, h)
-    else:
-        src, des = np.zeros(nx * ny * nz, bool), synth.design_column(nx, ny, nz, h)
-    fixed = np.ones(nx * ny * nz)
-    fixed[src] = 0.0
-    return des, fixed
+    return cavity.design_regions(cfg["nx"], cfg["ny"], cfg["nz"], cfg["h"],
+                                 cfg.get("bcs") == "quarter")
 
 
 class Optimizer:
@@ -139,7 +133,7 @@ class Optimizer:
         sopts = nc.default_opts(mixed=self.mixed, rtol_newton=self.state_rtol, ramp_steps=3)
         _, sinf = p.newton_solve(gam, self.x, sopts, check=False)
         phi, dphi = p.objective(self.x)
-        aopts = nc.default_opts(mixed=self.mixed, rtol_newton=self.adjoint_rtol)
+        aopts = nc.default_opts(mixed=self.mixed, rtol_adjoint=self.adjoint_rtol)
         lam, ainf = p.adjoint_solve(self.x, gam, -dphi, opts=aopts, check=False)
         sens = p.sensitivity(self.x, gam, lam)
         # chain rule of the filter (symmetric) on the design variables only

@@ -15,10 +15,15 @@ available, so design fields are generated:
     the solid density rho is converted to the paper's gamma = 1 - rho.
   * ``quarter``: the paper's quarter cavity (solid source block, design domain
     at 1 - v_f with small seeded noise, fluid elsewhere).
-The design column is the set of elements whose centroid has x, y in
-[0.25, 0.75] L and z in [0, 0.75 Lz].
+The regions (design column, quarter-cavity blocks) are defined in
+``cavity``, the package's statement of the problem set-up; this module only
+draws random fields on them.
 """
 import numpy as np
+
+from . import cavity as _cavity
+# the cavity regions, re-exported for the input generators' users
+from .cavity import QUARTER, design_column, elem_centroids, quarter_regions  # noqa: F401
 
 # name: (nx, ny, nz, h, Gr, Pr, patch mode, design generator, seed)
 WORKLOADS = {
@@ -53,27 +58,9 @@ WORKLOADS = {
                                      patch="none", bcs="quarter", design="quarter", seed=7,
                                      material=dict(alpha_max=1e5, q_alpha=8.0, q_f=0.881, Ck=1e-2)),
 }
-# Quarter-cavity geometry (fractions of the full unit cavity): heat-source block
-# 0.1 x 0.1 wide, 0.05 high at the centre of the bottom; design domain 0.75 x 0.75
-# wide and 0.75 high, sitting on top of the source block.
-QUARTER = dict(source_half=0.05, source_height=0.05, design_half=0.375, design_height=0.75,
-               s0=1e4, vf=0.05)
 # material parameters common to all workloads: RAMP q = 1, alpha_max = 1e4,
 # solid-to-fluid conductivity ratio 10 (Ck = k_f / k_s = 0.1)
 MATERIAL = dict(alpha_max=1e4, q_alpha=1.0, q_f=1.0, Ck=0.1)
-
-
-def elem_centroids(nx, ny, nz, h):
-    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
-    return np.stack([(i.ravel() + 0.5) * h, (j.ravel() + 0.5) * h, (k.ravel() + 0.5) * h], 1)
-
-
-def design_column(nx, ny, nz, h):
-    c = elem_centroids(nx, ny, nz, h)
-    Lx, Ly, Lz = nx * h, ny * h, nz * h
-    return ((c[:, 0] >= 0.25 * Lx) & (c[:, 0] <= 0.75 * Lx)
-            & (c[:, 1] >= 0.25 * Ly) & (c[:, 1] <= 0.75 * Ly)
-            & (c[:, 2] <= 0.75 * Lz))
 
 
 def box_filter3(a):
@@ -118,19 +105,6 @@ def fins(nx, ny, nz, h, seed):
     return gam
 
 
-def quarter_regions(nx, ny, nz, h):
-    """Source-block and design-domain element masks of the quarter cavity, whose
-    symmetry planes are the faces x = nx h and y = ny h."""
-    c = elem_centroids(nx, ny, nz, h)
-    Lx, Ly = nx * h, ny * h
-    q = QUARTER
-    near = lambda half: (c[:, 0] >= Lx - half) & (c[:, 1] >= Ly - half)
-    src = near(q["source_half"]) & (c[:, 2] <= q["source_height"])
-    des = (near(q["design_half"]) & (c[:, 2] > q["source_height"])
-           & (c[:, 2] <= q["source_height"] + q["design_height"]))
-    return src, des
-
-
 def quarter_design(nx, ny, nz, h, seed):
     """Solid source block (gamma = 0), the design domain at the volume fraction
     of the paper (gamma = 1 - v_f, the uniform start of an optimisation) with
@@ -145,13 +119,9 @@ def quarter_design(nx, ny, nz, h, seed):
 
 
 def source(name_or_cfg):
-    """Element heat source s_e: s0 in the source block of the quarter cavity."""
+    """Element heat source s_e of a workload (cavity.source)."""
     cfg = WORKLOADS[name_or_cfg] if isinstance(name_or_cfg, str) else name_or_cfg
-    s = np.zeros(cfg["nx"] * cfg["ny"] * cfg["nz"])
-    if cfg.get("bcs") == "quarter":
-        src, _ = quarter_regions(cfg["nx"], cfg["ny"], cfg["nz"], cfg["h"])
-        s[src] = QUARTER["s0"]
-    return s
+    return _cavity.source(cfg["nx"], cfg["ny"], cfg["nz"], cfg["h"], cfg.get("bcs") == "quarter")
 
 
 def material(name_or_cfg):

@@ -49,10 +49,10 @@ def test_default_opts(lib):
     from paper_1508_04596_gb300 import nc
     o = nc.default_opts()
     assert (o.rtol_newton, o.rtol_lin, o.restart, o.mixed) == (1e-8, 1e-5, 30, 1)
-    assert (o.galerkin, o.assembled) == (0, 0)
+    assert (o.galerkin, o.assembled, o.rtol_adjoint) == (0, 0, 1e-10)
 
 
-@pytest.mark.parametrize("struct,fill,last", [("SolveOpts", "nc_default_opts", "assembled"),
+@pytest.mark.parametrize("struct,fill,last", [("SolveOpts", "nc_default_opts", "rtol_adjoint"),
                                              ("MmaOpts", "nc_default_mma_opts", "df0_scale")])
 def test_option_structs_match_the_header(lib, struct, fill, last):
     """The ctypes mirrors of the option structs have the C layout: the library's

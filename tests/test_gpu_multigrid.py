@@ -120,6 +120,6 @@ def test_newton_with_galerkin_coarse_operators(nc):
     gq = nc.Problem(p, nc.cavity_bcs(nc.PATCH_FLUX, 1.0))
     for mixed in (0, 1):
         lam, info = gq.adjoint_solve(dev(xa), dev(ga), dev(-dphi),
-                                     opts=nc.default_opts(mixed=mixed, rtol_newton=1e-11,
+                                     opts=nc.default_opts(mixed=mixed, rtol_adjoint=1e-11,
                                                           galerkin=1))
         assert info["status"] == "NC_OK" and rel(host(lam), lam_o.ravel()) <= 1e-8, info

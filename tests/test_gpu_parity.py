@@ -250,7 +250,7 @@ def test_fins64_sampled_rows(nc, prec):
     rng = np.random.default_rng(22)
     v = rng.standard_normal((5, prob.g.Nn))
     dt = torch.float64 if prec == "f64" else torch.float32
-    tol = TOL64 * 10 if prec == "f64" else TOL32
+    tol = TOL64 if prec == "f64" else TOL32
     Jv = host(gp.jvp(dev(x, dt), dev(gam, dt), dev(v, dt)), (5, -1))
     JTw = host(gp.jtvp(dev(x, dt), dev(gam, dt), dev(v, dt)), (5, -1))
     nodes = rng.choice(prob.g.Nn, size=48, replace=False)
@@ -264,7 +264,8 @@ def test_fins64_sampled_rows(nc, prec):
     for kind, got in got_all:
         ref = sampled_rows(prob.g, prob.prm, x, gam, vm, nodes, kind)
         ref = np.where(prob.dmask[:, nodes], v[:, nodes], ref)
-        assert rel(got[:, nodes], ref) <= tol, kind
+        err = rel(got[:, nodes], ref)
+        assert err <= tol, (kind, err)
 
 
 def test_largest_config_sampled_rows(nc):
@@ -300,8 +301,10 @@ def test_largest_config_sampled_rows(nc):
     del X32, G32, V32
     X, Gm, V = dev(x), dev(gam), dev(v)
     gp.linearize(X, Gm)
-    assert rel(pick(gp.jvp_lin(V)), refs["jvp"]) <= TOL64 * 10
-    assert rel(pick(gp.jtvp_lin(V)), refs["jtvp"]) <= TOL64 * 10
+    err = rel(pick(gp.jvp_lin(V)), refs["jvp"])
+    assert err <= TOL64, ("jvp_lin", err)
+    err = rel(pick(gp.jtvp_lin(V)), refs["jtvp"])
+    assert err <= TOL64, ("jtvp_lin", err)
 
 
 def test_newton_matches_oracle_cfg0(nc):
@@ -323,9 +326,10 @@ def test_newton_matches_oracle_cfg0(nc):
 def test_adjoint_and_sensitivity_match_oracle(nc):
     """Flux-patch cavity at 8^3: adjoint solve and sensitivities against the
     oracle's direct adjoint (the adjoint at the oracle's converged state).  The
-    refinement stops on ||rhs - J^T lambda|| <= rtol ||rhs||, which bounds the
-    solution error by cond(J) rtol: at the default rtol 1e-8 the residual is
-    checked, and a solve to 1e-11 is compared with the oracle to 1e-8."""
+    refinement stops on ||rhs - J^T lambda|| <= rtol_adjoint ||rhs||, which bounds
+    the solution error by cond(J) rtol_adjoint: at the default 1e-10 the residual
+    is checked and the adjoint and the sensitivities are compared with the
+    oracle's to 1e-8; a solve to 1e-11 is compared to 1e-9."""
     n, Gr = 8, 1e4
     prob, bc = oracle_problem(n, n, n, 1.0 / n, Gr, 0.71, patch_mode="flux")
     gam = synth.smoothed_random(n, n, n, 1.0 / n, 3)
@@ -336,14 +340,17 @@ def test_adjoint_and_sensitivity_match_oracle(nc):
     p = nc.make_params(n, n, n, 1.0 / n, Gr, 0.71, **synth.MATERIAL)
     gp = nc.Problem(p, nc.cavity_bcs(nc.PATCH_FLUX, 1.0))
     for mixed in (0, 1):
-        _, info = gp.adjoint_solve(dev(xo), dev(gam), dev(-dphi),
-                                   opts=nc.default_opts(mixed=mixed))
-        assert info["res_final"] <= 1e-8 * info["res0"], info
         lam, info = gp.adjoint_solve(dev(xo), dev(gam), dev(-dphi),
-                                     opts=nc.default_opts(mixed=mixed, rtol_newton=1e-11))
+                                     opts=nc.default_opts(mixed=mixed))
+        assert info["res_final"] <= 1e-10 * info["res0"], info
         assert rel(host(lam), lam_o.ravel()) <= 1e-8, info
         sens = host(gp.sensitivity(dev(xo), dev(gam), lam))
         assert rel(sens, sens_o) <= 1e-8
+        lam, info = gp.adjoint_solve(dev(xo), dev(gam), dev(-dphi),
+                                     opts=nc.default_opts(mixed=mixed, rtol_adjoint=1e-11))
+        assert rel(host(lam), lam_o.ravel()) <= 1e-9, info
+        sens = host(gp.sensitivity(dev(xo), dev(gam), lam))
+        assert rel(sens, sens_o) <= 1e-9
 
 
 def test_errors_are_status_codes(nc):

@@ -40,7 +40,7 @@ def test_sensitivity_vs_fd_cavity96(nc):
     x = torch.zeros(prob.ndof, dtype=torch.float64, device="cuda")
     _, info = prob.newton_solve(gam, x, nc.default_opts(rtol_newton=1e-12, ramp_steps=3))
     phi, dphi = prob.objective(x)
-    lam, _ = prob.adjoint_solve(x, gam, -dphi, opts=nc.default_opts(rtol_newton=1e-12))
+    lam, _ = prob.adjoint_solve(x, gam, -dphi, opts=nc.default_opts(rtol_adjoint=1e-12))
     sens = prob.sensitivity(x, gam, lam).cpu().numpy()
     col = np.nonzero(synth.design_column(cfg["nx"], cfg["ny"], cfg["nz"], cfg["h"]))[0]
     top = col[np.argsort(-np.abs(sens[col]))[: max(64, len(col) // 100)]]
@@ -89,7 +89,7 @@ def test_gradient_matches_oracle_24(nc):
     prob = nc.Problem(p, nc.cavity_bcs(nc.PATCH_FLUX, 1.0))
     gam = dev(synth.smoothed_random(n, n, n, 1.0 / n, 3))
     for mixed in (1, 0):
-        opts = nc.default_opts(mixed=mixed, rtol_newton=1e-12, ramp_steps=3)
+        opts = nc.default_opts(mixed=mixed, rtol_newton=1e-12, rtol_adjoint=1e-12, ramp_steps=3)
         x = torch.zeros(prob.ndof, dtype=torch.float64, device="cuda")
         prob.newton_solve(gam, x, opts)
         phi, dphi = prob.objective(x)
@@ -150,14 +150,16 @@ def test_mixed_matches_fp64_32(nc):
     """32^3 cavity at Gr = 1e5: the mixed-precision Newton state agrees with the
     plain FP64 one to <= 1e-8 relative (Newton's quadratic convergence puts the
     state far inside its 1e-8 residual tolerance), and both adjoint solves meet
-    their 1e-8 residual tolerance.  The adjoint stops on the residual, which
-    bounds the solution error only by cond(J) x 1e-8, so the two adjoint
-    solutions are compared after solving both to 1e-11: <= 1e-8 relative."""
+    their default 1e-10 residual tolerance.  The adjoint stops on the residual,
+    which bounds the solution error only by cond(J) x 1e-10; the adjoint
+    solutions and the sensitivities of the two modes agree to <= 1e-8 relative,
+    and to <= 1e-9 after solving both adjoints to 1e-11."""
     n = 32
     p = nc.make_params(n, n, n, 1.0 / n, 1e5, 0.71, **synth.MATERIAL)
     prob = nc.Problem(p, nc.cavity_bcs(nc.PATCH_FLUX, 1.0))
     gam = dev(synth.smoothed_random(n, n, n, 1.0 / n, 8))
-    xs = []
+    rel = lambda a, b: (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item()
+    xs, lams, sens = [], [], []
     for mixed in (1, 0):
         opts = nc.default_opts(mixed=mixed, ramp_steps=3)
         x = torch.zeros(prob.ndof, dtype=torch.float64, device="cuda")
@@ -165,13 +167,17 @@ def test_mixed_matches_fp64_32(nc):
         assert info["status"] == "NC_OK"
         phi, dphi = prob.objective(x)
         lam, ainfo = prob.adjoint_solve(x, gam, -dphi, opts=opts)
-        assert ainfo["status"] == "NC_OK" and ainfo["res_final"] <= 1e-8 * ainfo["res0"]
+        assert ainfo["status"] == "NC_OK" and ainfo["res_final"] <= 1e-10 * ainfo["res0"]
         xs.append(x)
-    assert (torch.linalg.norm(xs[0] - xs[1]) / torch.linalg.norm(xs[1])).item() <= 1e-8
+        lams.append(lam)
+        sens.append(prob.sensitivity(x, gam, lam))
+    assert rel(xs[0], xs[1]) <= 1e-8
+    assert rel(lams[0], lams[1]) <= 1e-8
+    assert rel(sens[0], sens[1]) <= 1e-8
     _, dphi = prob.objective(xs[1])
-    ls = [prob.adjoint_solve(xs[1], gam, -dphi, opts=nc.default_opts(mixed=m, rtol_newton=1e-11))[0]
+    ls = [prob.adjoint_solve(xs[1], gam, -dphi, opts=nc.default_opts(mixed=m, rtol_adjoint=1e-11))[0]
           for m in (1, 0)]
-    assert (torch.linalg.norm(ls[0] - ls[1]) / torch.linalg.norm(ls[1])).item() <= 1e-8
+    assert rel(ls[0], ls[1]) <= 1e-9
 
 
 def test_newton_ramping_recovers(nc):

@@ -1,12 +1,16 @@
-"""The allocation-free J v (nc_jvp_static) against the context-based nc_jvp.
+"""The allocation-free J v (nc_jvp_static) against the context-based nc_jvp and
+against the oracle's assembled Jacobian.
 
 nc_jvp_static exists for callers that may not allocate device memory (an
 application whose memory pool owns the device, a plug-in whose host tracks every
 allocation, a loop that cannot afford cudaMalloc's synchronisation); it keeps its
 scratch in a fixed array inside the library.  This test calls it through the C
 ABI twice in a row -- the second call reuses the scratch the first one left
-behind -- and compares each result with nc_jvp on the same inputs, within the
-tolerances of the other parity tests.  It runs last in a collection so that a
+behind -- and compares each result with nc_jvp on the same inputs, and with the
+oracle's J v on two boundary-condition sets (the heated cavity with a patch held
+at T = 1, and a set with symmetry planes, a pinned pressure node and a
+flux-heated patch, which exercises every rule of the entry point's own
+boundary-flag kernel), within the tolerances of the other parity tests.  It runs last in a collection so that a
 failure here cannot hide another test's result.
 """
 import ctypes
@@ -70,3 +74,65 @@ def test_static_jvp_rejects_oversize(nc):
     t = torch.zeros(1, dtype=torch.float64, device="cuda")  # never touched
     assert call_static(nc, p, b, t, t, t, t, nc.NC_FP64) == 7  # NC_ERR_SIZE
     assert nc.lib.nc_status_string(7).startswith(b"problem larger")
+
+
+def _bc_sets(nc, nx, ny, nz):
+    from oracle import grid as G
+    cav = (nc.cavity_bcs(nc.PATCH_DIRICHLET, 1.0), G.BCs(patch_mode=G.PATCH_DIRICHLET))
+    pin = 3 + (nx + 1) * (2 + (ny + 1) * nz)  # a node on the top face
+    b = nc.BCs()
+    b.vel_bc[:] = [nc.VEL_NOSLIP, nc.VEL_SYMMETRY, nc.VEL_SYMMETRY, nc.VEL_NOSLIP,
+                   nc.VEL_NOSLIP, nc.VEL_FREE]
+    b.T_bc[:] = [nc.T_DIRICHLET, nc.T_ADIABATIC, nc.T_ADIABATIC, nc.T_DIRICHLET,
+                 nc.T_ADIABATIC, nc.T_DIRICHLET]
+    b.T_val[:] = [0.0] * 6
+    b.patch[:] = [1 / 3, 2 / 3, 1 / 3, 2 / 3]
+    b.patch_mode, b.patch_val, b.p_pin = nc.PATCH_FLUX, 1.0, pin
+    o = G.BCs(vel_bc=(G.NOSLIP, G.SYMMETRY, G.SYMMETRY, G.NOSLIP, G.NOSLIP, G.FREE),
+              T_bc=(G.DIRICHLET, G.ADIABATIC, G.ADIABATIC, G.DIRICHLET, G.ADIABATIC, G.DIRICHLET),
+              patch_mode=G.PATCH_FLUX, p_pin=pin)
+    return {"cavity": cav, "symmetry_pin_flux": (b, o)}
+
+
+@pytest.mark.parametrize("bcset", ["cavity", "symmetry_pin_flux"])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_static_jvp_matches_oracle_twice(nc, prec, bcset):
+    from paper_1508_04596_gb300 import synth
+    from tests.helpers import oracle_problem, random_bc_state
+    nx, ny, nz = 9, 7, 10
+    h = 1.0 / nx
+    b, ob = _bc_sets(nc, nx, ny, nz)[bcset]
+    p = nc.make_params(nx, ny, nz, h, 1e4, 0.71, **synth.MATERIAL)
+    prob, _ = oracle_problem(nx, ny, nz, h, 1e4, 0.71, bc=ob)
+    gam = synth.smoothed_random(nx, ny, nz, h, 5)
+    x = random_bc_state(prob, 6)
+    J = prob.jacobian(x, gam)
+    dt, code, tol = ((torch.float64, nc.NC_FP64, 1e-12) if prec == "f64"
+                     else (torch.float32, nc.NC_FP32, 2e-4))
+    xd = torch.tensor(x.ravel(), dtype=dt, device="cuda")
+    gd = torch.tensor(gam, dtype=dt, device="cuda")
+    rng = np.random.default_rng(10)
+    for call in range(2):
+        v = rng.standard_normal(prob.g.ndof)
+        out = torch.full_like(xd, float("nan"))
+        assert call_static(nc, p, b, xd, gd, torch.tensor(v, dtype=dt, device="cuda"), out,
+                           code) == 0
+        torch.cuda.synchronize()
+        ref = J @ v
+        err = float(np.linalg.norm(out.double().cpu().numpy() - ref) / np.linalg.norm(ref))
+        assert err <= tol, (call, err)
+
+
+def test_static_jvp_rejects_invalid_arguments(nc):
+    """The checks of nc_setup: a patch mode out of range, a non-finite Gr, a
+    negative alpha_max and a dimension too large to form its products are
+    NC_ERR_ARG before anything is launched."""
+    t = torch.zeros(1, dtype=torch.float64, device="cuda")  # never touched
+    b = nc.cavity_bcs()
+    b.patch_mode = 3
+    assert call_static(nc, nc.make_params(4, 4, 4, 0.25, 1e3, 0.71), b, t, t, t, t,
+                       nc.NC_FP64) == 1
+    for p in (nc.make_params(4, 4, 4, 0.25, float("inf"), 0.71),
+              nc.make_params(4, 4, 4, 0.25, 1e3, 0.71, alpha_max=-1.0),
+              nc.make_params(2 ** 31 - 1, 4, 4, 0.25, 1e3, 0.71)):
+        assert call_static(nc, p, nc.cavity_bcs(), t, t, t, t, nc.NC_FP64) == 1
