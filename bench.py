@@ -52,7 +52,7 @@ PEAK_SOURCE = ("unit counts x max SM clock: 152 SMs x 128 FP32 lanes (2 FP64 FMA
 # the capture was taken with (their SHA-256 is recorded beside the figure).
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_elem_lin_cached_tall192x192x384_traffic.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1508_04596_gb300", "csrc", f)
-                  for f in ("nc_kernels.cu", "nc_element.cuh", "nc_internal.cuh")]
+                  for f in ("nc_kernels.cu", "nc_element.cuh")]
 
 
 def parse():
@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--solve-workload", default=None,
                     help="workload of the state/adjoint design-iteration timing (default: --workload)")
+    ap.add_argument("--jv-only", action="store_true",
+                    help="only the timed J v step (profiling runs: no end-to-end, operator, "
+                         "assembled or vector measurements)")
     ap.add_argument("--vectors-only", default=None, choices=["f32", "f64", "both"],
                     help="only time the FGMRES orthogonalisation step (the HBM-side kernels) "
                          "and print its JSON (profiling runs)")
@@ -388,6 +391,12 @@ def run_ours(args, rank, world):
             "peak_source": PEAK_SOURCE,
             "peak_probe": extra["alu_probe"][args.prec]["tflops"],
             "frac_of_probe": round(achieved / extra["alu_probe"][args.prec]["tflops"], 4)}
+
+    if args.jv_only:
+        line = {"metric": "J·v GDOF/s (profiling run, --jv-only)", "value": round(value, 4),
+                "unit": "GDOF/s", "ms_per_step": round(t_step, 4), "dtype": args.prec,
+                "config": {"workload": args.workload}, "roofline": roof}
+        return line if rank == 0 else None
 
     # --- end to end through the C ABI with host buffers
     xh = xj.cpu().pin_memory()

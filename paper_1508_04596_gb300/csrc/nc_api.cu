@@ -192,6 +192,7 @@ void nc_destroy(nc_ctx* ctx) {
   cudaFree(ctx->src64);
   cudaFree(ctx->kry.V);
   cudaFree(ctx->kry.Z);
+  cudaFree(ctx->kry.Zf);
   cudaFree(ctx->kry.w);
   cudaFree(ctx->kry.hcol);
   cudaFree(ctx->kry.y);

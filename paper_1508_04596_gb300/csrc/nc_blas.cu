@@ -440,6 +440,42 @@ __global__ void k_maxpy(long long n, int k, const R* __restrict__ X, long long l
   });
 }
 
+// y -= sign * sum_i coef[i] X_i with FP32 columns and an FP64 y (FP64 arithmetic,
+// the same order of operations as k_maxpy<double> on the cast columns)
+template <bool VEC>
+__global__ void k_maxpy_f32x(long long n, int k, const float* __restrict__ X, long long ld,
+                             const double* __restrict__ coef, double sign,
+                             double* __restrict__ y) {
+  __shared__ double cf[MAX_RESTART + 1];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) cf[i] = sign * coef[i];
+  __syncthreads();
+  chunk_loop(n, [&](long long c) {
+    double a[4];
+    ld4<double, VEC>(y, c, a);
+    int q = 0;
+    for (; q + 4 <= k; q += 4) {
+      float xv[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) ld4<float, VEC>(X + (q + r) * ld, c, xv[r]);
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] -= cf[q + r] * (double)xv[r][u];
+    }
+    for (; q < k; ++q) {
+      float xv[4];
+      ld4<float, VEC>(X + q * ld, c, xv);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] -= cf[q] * (double)xv[u];
+    }
+    st4<double, VEC>(y, c, a);
+  }, [&](long long i) {
+    double a = y[i];
+    for (int q = 0; q < k; ++q) a -= cf[q] * (double)X[q * ld + i];
+    y[i] = a;
+  });
+}
+
 // Second classical Gram-Schmidt pass with the normalisation folded in:
 // y <- (y - sum_i h_i X_i) / nw,  nw = sqrt(q - sum_i h_i^2)  with q = ||y||^2 on
 // entry (h and q from one fused multi-dot; X orthonormal, so nw is the norm of
@@ -617,6 +653,13 @@ void vmaxpy_scale(long long n, int k, const R* X, long long ld, const double* h,
     k_maxpy_scale<R, true><<<map_blocks(n), VT, 0, s>>>(n, k, X, ld, h, q, nw_out, y);
   else
     k_maxpy_scale<R, false><<<map_blocks(n), VT, 0, s>>>(n, k, X, ld, h, q, nw_out, y);
+}
+void vmaxpy_f32x(long long n, int k, const float* X, long long ld, const double* coef,
+                 double sign, double* y, cudaStream_t s) {
+  if (mv_aligned(X, ld) && al16(y))
+    k_maxpy_f32x<true><<<map_blocks(n), VT, 0, s>>>(n, k, X, ld, coef, sign, y);
+  else
+    k_maxpy_f32x<false><<<map_blocks(n), VT, 0, s>>>(n, k, X, ld, coef, sign, y);
 }
 void dev_sqrt_store(const double* in, double* out, cudaStream_t s) {
   k_sqrt_store<<<1, 1, 0, s>>>(in, out);

@@ -76,7 +76,9 @@ struct Level {
 struct Krylov {
   int m = 0;
   double* V = nullptr;   // (m+1) x ndof
-  double* Z = nullptr;   // m x ndof
+  double* Z = nullptr;   // m x ndof: preconditioned directions (FP64 solves)
+  float* Zf = nullptr;   // m x ndof: the same in mixed solves, where the V-cycle that
+                         // produces them runs in FP32, so FP32 storage is exact
   double* w = nullptr;
   double* hcol = nullptr;  // device, 2*(m+2)
   double* y = nullptr;     // device, m
@@ -187,6 +189,10 @@ void vmdot_self(long long n, int k, const R* X, long long ld, const R* y, double
 template <typename R>
 void vmaxpy(long long n, int k, const R* X, long long ld, const double* coef, double sign, R* y,
             cudaStream_t s);
+// y -= sign * sum_i coef[i] X_i for FP32 columns X and an FP64 y, accumulated in
+// FP64 (each FP32 entry is exact in FP64, so this equals vmaxpy on the FP64 casts)
+void vmaxpy_f32x(long long n, int k, const float* X, long long ld, const double* coef,
+                 double sign, double* y, cudaStream_t s);
 // y <- (y - sum_i h[i] X_i) / nw with nw = sqrt(*q - sum_i h[i]^2) (X orthonormal,
 // *q = ||y||^2 before the update); nw -> *nw_out.  The second pass of classical
 // Gram-Schmidt with its normalisation.

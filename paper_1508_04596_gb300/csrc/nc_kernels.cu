@@ -4,6 +4,9 @@
 // its 40 element rows to a scratch array Y[(f*8 + a)*E + e]; one thread per node
 // then sums the rows of its (up to) eight elements in the fixed local order
 // a = 0..7.  No atomics, so results are bitwise reproducible.
+#include <type_traits>
+
+#include "nc_element_f2.cuh"
 #include "nc_internal.cuh"
 
 namespace nc {
@@ -87,7 +90,8 @@ __global__ void __launch_bounds__(ELEM_THREADS) k_elem_res(LevelDev d, ElemConst
 
 // Three blocks per SM (at most 168 registers, a few spilled): 12 warps per SM hide
 // more latency than 8 at 255 registers; measured 9.6 % faster in FP32 and
-// unchanged in FP64.
+// unchanged in FP64.  FP32 takes the packed-pair element routines (two lanes of
+// FP32 arithmetic per instruction).
 template <typename R, bool TRANSPOSE>
 __global__ void __launch_bounds__(ELEM_THREADS, 3) k_elem_lin(LevelDev d, ElemConst<R> c,
                                                            const R* __restrict__ x,
@@ -100,10 +104,17 @@ __global__ void __launch_bounds__(ELEM_THREADS, 3) k_elem_lin(LevelDev d, ElemCo
   load_elem(d, x, e, xe, false);
   load_elem(d, v, e, ve, true);  // Dirichlet columns removed
   const R g = gam[e], s = src ? src[e] : R(0);
-  if (TRANSPOSE)
-    elem_jtvp<R>(xe, ve, g, s, c, out);
-  else
-    elem_jvp<R>(xe, ve, g, s, c, out);
+  if constexpr (std::is_same<R, float>::value) {
+    if (TRANSPOSE)
+      elem_jtvp_f2(xe, ve, g, s, c, out);
+    else
+      elem_jvp_f2(xe, ve, g, s, c, out);
+  } else {
+    if (TRANSPOSE)
+      elem_jtvp<R>(xe, ve, g, s, c, out);
+    else
+      elem_jvp<R>(xe, ve, g, s, c, out);
+  }
   store_elem(d.E, e, out, Y);
 }
 

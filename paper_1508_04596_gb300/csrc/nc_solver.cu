@@ -350,9 +350,10 @@ void capture_cycle(nc_ctx* ctx, const LinSolve& ls, const nc_solve_opts& o, Cycl
   cudaGraphDestroy(graph);
 }
 
-// z = M^-1 v (one V-cycle in the chosen precision)
+// z = M^-1 v (one V-cycle in the chosen precision); z is the FP64 column z64
+// (FP64 solves) or the FP32 column z32 (mixed solves, whose cycle output is FP32)
 void precond(nc_ctx* ctx, const LinSolve& ls, const nc_solve_opts& o, const CycleGraph& g,
-             const double* v, double* z, cudaStream_t s) {
+             const double* v, double* z64, float* z32, cudaStream_t s) {
   Level& L = ctx->lv[0];
   const long long n = 5 * L.d.Nn;
   if (ls.mixed)
@@ -364,9 +365,16 @@ void precond(nc_ctx* ctx, const LinSolve& ls, const nc_solve_opts& o, const Cycl
   else
     run_cycle(ctx, ls, o, s);
   if (ls.mixed)
-    vcast(n, (const float*)L.f32.z, z, s);
+    vcopy(n, (const float*)L.f32.z, z32, s);
   else
-    vcopy(n, (const double*)L.f64.z, z, s);
+    vcopy(n, (const double*)L.f64.z, z64, s);
+}
+
+// out = A z for an FP32 z (mixed solves: the FP32 product, its result in FP64)
+void apply_A32(nc_ctx* ctx, const LinSolve& ls, const float* z, double* out, cudaStream_t s) {
+  Level& L = ctx->lv[0];
+  level_apply<float>(ctx, 0, ls.tr, z, L.f32.r, s);
+  vcast(5 * L.d.Nn, (const float*)L.f32.r, out, s);
 }
 
 // out = A v with the linear solve's operator (FP32 product in mixed mode)
@@ -424,7 +432,8 @@ nc_status fgmres(nc_ctx* ctx, const LinSolve& ls, const nc_solve_opts& o, const 
   const int m = ctx->kry.m;
   const long long ld = mv_ld(n);
   double* V = ctx->kry.V;
-  double* Z = ctx->kry.Z;
+  double* Z = ctx->kry.Z;    // FP64 solves
+  float* Zf = ctx->kry.Zf;   // mixed solves
   double* hc = ctx->kry.hcol;
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hh(2 * (m + 2) + 1);
   vzero(n, x, s);
@@ -454,10 +463,16 @@ nc_status fgmres(nc_ctx* ctx, const LinSolve& ls, const nc_solve_opts& o, const 
     bool done = false;
     for (; j < m && total < o.max_lin; ++j) {
       double* vj = V + j * ld;
-      double* zj = Z + j * ld;
       double* w = V + (j + 1) * ld;
-      precond(ctx, ls, o, graph, vj, zj, s);
-      apply_A(ctx, ls, zj, w, s);
+      if (ls.mixed) {
+        float* zj = Zf + j * ld;
+        precond(ctx, ls, o, graph, vj, nullptr, zj, s);
+        apply_A32(ctx, ls, zj, w, s);
+      } else {
+        double* zj = Z + j * ld;
+        precond(ctx, ls, o, graph, vj, zj, nullptr, s);
+        apply_A(ctx, ls, zj, w, s);
+      }
       cgs2(n, j + 1, (const double*)V, ld, w, hc, m + 2, ctx->partial, s);
       // one device-to-host read per iteration: both Gram-Schmidt columns and ||w||
       if ((st = read_scalar(ctx, hc, hh.data(), 2 * (m + 2) + 1, s)) != NC_OK) return st;
@@ -499,7 +514,10 @@ nc_status fgmres(nc_ctx* ctx, const LinSolve& ls, const nc_solve_opts& o, const 
       if ((st = cuda_check(ctx, cudaMemcpyAsync(ctx->kry.y, y.data(), sizeof(double) * j,
                                                 cudaMemcpyHostToDevice, s), "upload y")) != NC_OK)
         return st;
-      vmaxpy(n, j, (const double*)Z, ld, ctx->kry.y, -1.0, x, s);
+      if (ls.mixed)
+        vmaxpy_f32x(n, j, (const float*)Zf, ld, ctx->kry.y, -1.0, x, s);
+      else
+        vmaxpy(n, j, (const double*)Z, ld, ctx->kry.y, -1.0, x, s);
       if ((st = cuda_check(ctx, cudaStreamSynchronize(s), "fgmres sync")) != NC_OK) return st;
     }
     first = false;
@@ -529,14 +547,21 @@ nc_status prepare(nc_ctx* ctx, const nc_solve_opts& o, int nlev, bool mixed) {
   if (ctx->kry.m < o.restart) {
     cudaFree(ctx->kry.V);
     cudaFree(ctx->kry.Z);
+    cudaFree(ctx->kry.Zf);
     ctx->kry.V = ctx->kry.Z = nullptr;
+    ctx->kry.Zf = nullptr;
     ctx->kry.m = 0;
   }
   if (!ctx->kry.V) {
-    if ((st = alloc(ctx, &ctx->kry.V, (long long)(o.restart + 1) * mv_ld(n))) != NC_OK ||
-        (st = alloc(ctx, &ctx->kry.Z, (long long)o.restart * mv_ld(n))) != NC_OK)
-      return st;
+    if ((st = alloc(ctx, &ctx->kry.V, (long long)(o.restart + 1) * mv_ld(n))) != NC_OK) return st;
     ctx->kry.m = o.restart;
+  }
+  // the preconditioned directions in the precision of the cycle that makes them
+  // (allocated per mode at its first solve, sized by the current restart)
+  if (mixed) {
+    if ((st = alloc(ctx, &ctx->kry.Zf, (long long)ctx->kry.m * mv_ld(n))) != NC_OK) return st;
+  } else {
+    if ((st = alloc(ctx, &ctx->kry.Z, (long long)ctx->kry.m * mv_ld(n))) != NC_OK) return st;
   }
   if ((st = alloc(ctx, &ctx->kry.w, n)) != NC_OK ||
       (st = alloc(ctx, &ctx->kry.hcol, 2LL * (MAX_RESTART + 2) + 1)) != NC_OK ||

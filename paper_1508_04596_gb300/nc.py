@@ -387,7 +387,9 @@ class Problem:
         solution, prolonged, starts the solve on the next finer grid; x receives
         the solution on this grid.  coarse_opts (default opts) apply to the
         coarser solves.  Returns (x, info) of the final solve, with
-        info["levels"] reporting the coarser ones (coarsest first)."""
+        info["levels"] reporting the coarser ones (coarsest first).  A coarser
+        solve that does not converge is not prolonged: the next finer grid then
+        starts from zero, and its entry in info["levels"] has prolonged=False."""
         chain, gams = [self], [gam]
         while True:
             c = chain[-1].coarse_problem()
@@ -400,10 +402,14 @@ class Problem:
         for k in range(len(chain) - 1, 0, -1):
             _, inf = chain[k].newton_solve(gams[k], xs, coarse_opts or opts, stream, check=False)
             pk = chain[k].params
+            ok = inf["status"] == "NC_OK"
             levels.append(dict(dims=(pk.nx, pk.ny, pk.nz), status=inf["status"],
                                newton_its=inf["newton_its"], lin_its=inf["lin_its_total"],
-                               seconds=inf["seconds"]))
-            xs = chain[k - 1].prolong(xs, stream)
+                               seconds=inf["seconds"], prolonged=ok))
+            if ok:
+                xs = chain[k - 1].prolong(xs, stream)
+            else:  # a failed coarse state would only mislead the finer solve
+                xs = torch.zeros(chain[k - 1].ndof, dtype=torch.float64, device=x.device)
             chain[k].close()  # free the coarser context before the finer solve
         x.copy_(xs)
         del xs

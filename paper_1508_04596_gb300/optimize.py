@@ -77,6 +77,7 @@ class Optimizer:
         self.step = -1
         self.x = None
         self.f0_scale = None
+        self.schedule = None  # (iters, steps) of the run's continuation schedule
 
     _TENSORS = ("rho", "xold1", "xold2", "low", "upp", "x")
 
@@ -85,7 +86,7 @@ class Optimizer:
         d = {k: getattr(self, k).detach().cpu() for k in self._TENSORS if getattr(self, k) is not None}
         d.update(workload=self.workload, over=dict(self.over), vf=self.vf, move=self.move,
                  mixed=self.mixed, state_rtol=self.state_rtol, adjoint_rtol=self.adjoint_rtol,
-                 k=self.k, step=self.step, f0_scale=self.f0_scale)
+                 k=self.k, step=self.step, f0_scale=self.f0_scale, schedule=self.schedule)
         return d
 
     def save(self, path):
@@ -100,6 +101,7 @@ class Optimizer:
             if k in d:
                 setattr(opt, k, d[k].to("cuda"))
         opt.k, opt.f0_scale = d["k"], d["f0_scale"]
+        opt.schedule = tuple(d["schedule"]) if d.get("schedule") else None
         if d["step"] >= 0:
             x = opt.x
             opt.set_step(d["step"])
@@ -155,21 +157,31 @@ class Optimizer:
                 "s": round(time.perf_counter() - t0, 4)}
 
 
-def run(workload, iters, steps=5, log=print, checkpoint=None, every=10, resume=None, **kw):
+def run(workload, iters, steps=5, log=print, checkpoint=None, every=10, resume=None,
+        stop_after=None, **kw):
     """`iters` design iterations in total over the first `steps` continuation
     steps; with `resume`, continue the run saved there (its iterations count
     towards `iters`); with `checkpoint`, save the run there every `every`
-    iterations and at the end."""
+    iterations and at the end; with `stop_after`, stop once that many iterations
+    are done in total (the schedule is still the one of `iters` and `steps`, so
+    the run can be split over several jobs and resumed)."""
     opt = Optimizer.load(resume) if resume else Optimizer(workload, **kw)
+    # the continuation step of iteration k depends on iters and steps: a resumed
+    # run must use the schedule it was saved with, or it would jump to another step
+    if opt.schedule is not None and opt.schedule != (iters, steps):
+        raise ValueError("the run in %s was saved with iters=%d, steps=%d; resume it with the same "
+                         "values (got iters=%d, steps=%d)" % ((resume,) + opt.schedule + (iters, steps)))
+    opt.schedule = (iters, steps)
     per = max(1, iters // steps)
+    end = iters if stop_after is None else min(iters, stop_after)
     hist = []
-    while opt.k < iters:
+    while opt.k < end:
         opt.set_step(min(opt.k // per, steps - 1, len(CONTINUATION) - 1))
         r = opt.iterate()
         hist.append(r)
         if log:
             log(json.dumps(r))
-        if checkpoint and (opt.k % every == 0 or opt.k == iters):
+        if checkpoint and (opt.k % every == 0 or opt.k == end):
             opt.save(checkpoint)
     return opt, hist
 
@@ -186,6 +198,8 @@ def main(argv=None):
     ap.add_argument("--checkpoint", help="save the run here (every --every iterations and at the end)")
     ap.add_argument("--every", type=int, default=10)
     ap.add_argument("--resume", help="continue the run saved in this file")
+    ap.add_argument("--stop-after", type=int, help="stop after this many iterations in total "
+                    "(with --checkpoint, to resume later with the same --iters and --steps)")
     a = ap.parse_args(argv)
     over = {}
     if a.nx:
@@ -193,7 +207,7 @@ def main(argv=None):
         over = dict(nx=a.nx, ny=a.ny or a.nx, nz=a.nz or a.nx)
         over["h"] = cfg["h"] * cfg["nz"] / over["nz"]
     run(a.workload, a.iters, a.steps, checkpoint=a.checkpoint, every=a.every, resume=a.resume,
-        mixed=0 if a.fp64 else 1, **over)
+        stop_after=a.stop_after, mixed=0 if a.fp64 else 1, **over)
 
 
 if __name__ == "__main__":

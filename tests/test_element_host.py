@@ -3,7 +3,8 @@ without a GPU: the element tangent against central differences of the element
 residual, its transpose, diagonal, linearisation-store and design-sensitivity
 variants against it (tests/host/element_consistency_check.cpp), and the
 specialised element columns of the assembled Jacobian against the general
-products (tests/host/element_columns_check.cpp)."""
+products (tests/host/element_columns_check.cpp), and the packed-pair FP32
+products against the scalar ones (tests/host/element_pairs_check.cpp)."""
 import os
 import shutil
 import subprocess
@@ -13,7 +14,8 @@ import pytest
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-@pytest.mark.parametrize("prog", ["element_consistency_check", "element_columns_check"])
+@pytest.mark.parametrize("prog", ["element_consistency_check", "element_columns_check",
+                                  "element_pairs_check"])
 def test_element_routines_on_the_host(tmp_path, prog):
     cxx = shutil.which("g++") or shutil.which("c++")
     if cxx is None:

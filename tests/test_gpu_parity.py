@@ -132,7 +132,17 @@ def test_linearised_products_fp64(nc, c):
         assert rel(host(gp.jtvp_lin(dev(v))), J.T @ v) <= TOL64
 
 
-@pytest.mark.parametrize("c", CASES)
+# grids at least a warp of elements wide, ragged in x and y, a single element
+# layer, and the flux patch
+WIDE_CASES = [
+    dict(nx=32, ny=4, nz=2, Gr=1e4, patch="dirichlet", seed=11),
+    dict(nx=40, ny=5, nz=3, Gr=1e5, patch="flux", seed=12),
+    dict(nx=37, ny=9, nz=1, Gr=1e3, patch="dirichlet", seed=13),
+    dict(nx=64, ny=6, nz=2, Gr=1e4, patch="flux", seed=14),
+]
+
+
+@pytest.mark.parametrize("c", CASES + WIDE_CASES)
 def test_fp32_operators(nc, c):
     prob, bc, gp, gam, x = make_pair(nc, c)
     J = prob.jacobian(x, gam)
@@ -201,22 +211,22 @@ def test_quarter_cavity_operators(nc):
 
 def test_quarter_cavity_newton_matches_oracle(nc):
     """Quarter cavity with the source block: Newton (FP64 and mixed) against the
-    oracle's direct-solve Newton.  Velocity, temperature and the thermal
-    compliance agree to 1e-8; the pressure is compared on nodes that touch a
-    fluid element -- inside the solid block (alpha = 1e5) the pressure is nearly
-    undetermined by the discrete equations and differs between solvers by
-    round-off amplified through that near-singular mode."""
+    oracle's direct-solve Newton, the whole state (all five fields at every
+    node, the solid block's pressure included) to 1e-8 relative, and the thermal
+    compliance to 1e-10.  The pressure is the least damped field of the residual
+    (a residual reduction of 1e-10 leaves about 1e-7 in p, 1e-9 in u and T), so
+    both solves go to 1e-12; the oracle's own direct solves with three column
+    orderings and a dense solve agree to 1e-15 there, so the pressure is fully
+    determined by the discrete equations."""
     prob, bc, gp, gam = quarter_pair(nc)
-    xo, _ = S.newton(prob, gam, np.zeros((5, prob.g.Nn)), rtol=1e-12)
+    xo, _ = S.newton(prob, gam, np.zeros((5, prob.g.Nn)), rtol=1e-13)
     fo, _ = S.objective(prob, bc, xo)
-    fluid_nodes = np.zeros(prob.g.Nn, bool)
-    fluid_nodes[prob.conn[gam > 0.5].ravel()] = True
     for mixed in (0, 1):
         x = torch.zeros(gp.ndof, dtype=torch.float64, device="cuda")
-        _, info = gp.newton_solve(dev(gam), x, nc.default_opts(mixed=mixed, rtol_newton=1e-10))
+        _, info = gp.newton_solve(dev(gam), x, nc.default_opts(mixed=mixed, rtol_newton=1e-12))
         xh = host(x, (5, -1))
-        assert rel(xh[[0, 1, 2, 4]], xo[[0, 1, 2, 4]]) <= 1e-8, info
-        assert rel(xh[3, fluid_nodes], xo[3, fluid_nodes]) <= 1e-7, info
+        err = rel(xh, xo)
+        assert err <= 1e-8, (mixed, err, info)
         f, _ = gp.objective(x)
         assert f == pytest.approx(fo, rel=1e-10)
 

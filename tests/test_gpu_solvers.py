@@ -214,16 +214,16 @@ def test_optimisation_loop_quarter_cavity(nc):
 
 
 def test_optimisation_checkpoint_resume(nc, tmp_path):
-    """Checkpoint / resume of the optimisation run: 2 iterations, a checkpoint,
-    then 2 more in a fresh optimiser loaded from it (crossing a continuation
-    step) give the same design, state and MMA history, bit for bit, as 4
-    iterations straight."""
+    """Checkpoint / resume of the optimisation run: a 4-iteration, 2-step run
+    stopped after 2 iterations with a checkpoint, then resumed in a fresh
+    optimiser loaded from it (crossing a continuation step), gives the same
+    design, state and MMA history, bit for bit, as 4 iterations straight."""
     from paper_1508_04596_gb300 import optimize
     kw = dict(nx=8, ny=8, nz=16, h=1.0 / 16)
     name = "quarter80x80x160_gr1e3"
     a, ha = optimize.run(name, 4, steps=2, log=None, **kw)
     ck = str(tmp_path / "run.pt")
-    optimize.run(name, 2, steps=1, log=None, checkpoint=ck, **kw)
+    optimize.run(name, 4, steps=2, log=None, checkpoint=ck, stop_after=2, **kw)
     b, hb = optimize.run(name, 4, steps=2, log=None, resume=ck)
     assert b.k == 4 and b.step == 1 and len(hb) == 2
     assert [r["phi"] for r in hb] == [r["phi"] for r in ha[2:]]

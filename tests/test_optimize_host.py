@@ -12,6 +12,7 @@ class FakeOptimizer:
 
     def __init__(self, workload, **kw):
         self.k, self.step, self.steps_seen = 0, -1, []
+        self.schedule = None
 
     def set_step(self, step):
         self.step = step
@@ -22,12 +23,12 @@ class FakeOptimizer:
         return {"iter": self.k, "step": self.step}
 
     def save(self, path):
-        FakeOptimizer.saved[path] = (self.k, self.step, list(self.steps_seen))
+        FakeOptimizer.saved[path] = (self.k, self.step, list(self.steps_seen), self.schedule)
 
     @classmethod
     def load(cls, path):
         o = cls("x")
-        o.k, o.step, o.steps_seen = FakeOptimizer.saved[path]
+        o.k, o.step, o.steps_seen, o.schedule = FakeOptimizer.saved[path]
         o.steps_seen = list(o.steps_seen)
         return o
 
@@ -55,7 +56,17 @@ def test_continuation_schedule(optimize):
 def test_checkpoint_every_and_resume(optimize):
     opt, _ = optimize.run("w", 4, steps=2, log=None, checkpoint="ck", every=3)
     assert FakeOptimizer.saved["ck"][0] == 4  # saved at iteration 3, then at the end
-    optimize.run("w", 2, steps=1, log=None, checkpoint="half")
+    optimize.run("w", 4, steps=2, log=None, checkpoint="half", stop_after=2)
+    assert FakeOptimizer.saved["half"] == (2, 0, [0, 0], (4, 2))
     b, hist = optimize.run("w", 4, steps=2, log=None, resume="half")
     assert b.k == 4 and len(hist) == 2
     assert b.steps_seen == opt.steps_seen == [0, 0, 1, 1]
+
+
+def test_resume_with_another_schedule_is_refused(optimize):
+    """The continuation step of iteration k depends on (iters, steps): a run saved
+    with one schedule and resumed with another would jump to a different step."""
+    optimize.run("w", 2, steps=1, log=None, checkpoint="c1")
+    assert FakeOptimizer.saved["c1"][3] == (2, 1)
+    with pytest.raises(ValueError, match="iters=2, steps=1"):
+        optimize.run("w", 4, steps=2, log=None, resume="c1")

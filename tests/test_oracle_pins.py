@@ -167,6 +167,39 @@ def test_dense_brute_force_newton():
         assert np.allclose(d_dense, d_sparse, rtol=1e-10, atol=1e-12 * np.abs(d_dense).max())
 
 
+def test_quarter_cavity_pressure_is_determined():
+    """Sec. 6.1 quarter cavity (symmetry planes, closed walls, pressure pinned at
+    one node, a solid heat-source block with s0 = 1e4 and alpha = 1e5): the
+    discrete pressure, inside the solid block included, is fixed by the
+    equations -- Newton with three different sparse-LU column orderings and with
+    a dense solve reaches the same state to round-off in every field."""
+    from paper_1508_04596_gb300 import cavity
+    n = 6
+    nx, ny, nz, h = n, n, 2 * n, 1.0 / (2 * n)
+    pin = (nx + 1) * (ny + 1) * nz
+    bc = G.BCs(vel_bc=(G.NOSLIP, G.SYMMETRY, G.NOSLIP, G.SYMMETRY, G.NOSLIP, G.NOSLIP),
+               T_bc=(G.DIRICHLET, G.ADIABATIC, G.DIRICHLET, G.ADIABATIC, G.ADIABATIC, G.DIRICHLET),
+               patch_mode=G.PATCH_NONE, p_pin=pin)
+    se = cavity.source(nx, ny, nz, h, True)
+    mat = synth.material("quarter80x80x160_gr1e3")
+    g, bc, prob = make(nx, ny, nz, h, Gr=1e3, Pr=1.0, bc=bc, se=se, **mat)
+    gam = synth.quarter_design(nx, ny, nz, h, 3)
+    assert (gam == 0).sum() >= 1 and se.sum() > 0
+    sols = []
+    for spec in ("COLAMD", "NATURAL", "MMD_AT_PLUS_A", "dense"):
+        if spec == "dense":
+            ls = lambda J, b: np.linalg.solve(J.toarray(), b)
+        else:
+            ls = lambda J, b, spec=spec: spla.splu(J.tocsc(), permc_spec=spec).solve(b)
+        x, _ = S.newton(prob, gam, np.zeros((5, g.Nn)), rtol=1e-13, linsolve=ls)
+        sols.append(x)
+    solid = np.zeros(g.Nn, bool)
+    solid[prob.conn[gam < 0.5].ravel()] = True
+    for x in sols[1:]:
+        assert np.linalg.norm(x - sols[0]) <= 1e-12 * np.linalg.norm(sols[0])
+        assert np.abs(x[3, solid] - sols[0][3, solid]).max() <= 1e-12 * np.abs(sols[0][3]).max()
+
+
 # ---------------------------------------------------------------- exact solutions
 def hydrostatic_case(Gr, Pr, T0, nx=5, ny=4, nz=6, h=0.2):
     bc = G.BCs(T_bc=(G.DIRICHLET,) * 6, T_val=(T0,) * 6, patch_mode=G.PATCH_DIRICHLET,

@@ -37,10 +37,13 @@ class FakeProblem:
         FakeProblem.log.append(("coarsen", self.n))
         return g[: (self.n // 2) ** 3]
 
+    fail = ()  # grid sizes whose solve fails
+
     def newton_solve(self, gam, x, opts=None, stream=None, check=True):
         FakeProblem.log.append(("solve", self.n, float(x.sum())))
         x.fill_(float(self.n))  # "the solution on this grid"
-        return x, {"status": "NC_OK", "newton_its": 1, "lin_its_total": 2, "seconds": 0.0}
+        st = "NC_ERR_MAXIT" if self.n in FakeProblem.fail else "NC_OK"
+        return x, {"status": st, "newton_its": 1, "lin_its_total": 2, "seconds": 0.0}
 
     def prolong(self, xc, stream=None):
         FakeProblem.log.append(("prolong", self.n, float(xc[0])))
@@ -62,3 +65,22 @@ def test_sequenced_order(nc):
         ("solve", 4, 2.0 * 5 * 5 ** 3), ("prolong", 8, 4.0), ("close", 4),
         ("solve", 8, 4.0 * 5 * 9 ** 3)]
     assert [lv["dims"] for lv in info["levels"]] == [(2, 2, 2), (4, 4, 4)]
+
+
+def test_failed_coarse_solve_is_not_prolonged(nc):
+    """A coarser solve that does not converge does not seed the finer one: the
+    next finer grid starts from zero and the level reports prolonged=False."""
+    FakeProblem.log, FakeProblem.fail = [], (2,)
+    try:
+        fine = FakeProblem(8, 3)
+        x = torch.zeros(fine.ndof, dtype=torch.float64)
+        _, info = nc.Problem.newton_solve_sequenced(fine, torch.ones(8 ** 3, dtype=torch.float64), x)
+    finally:
+        FakeProblem.fail = ()
+    assert FakeProblem.log == [
+        ("coarsen", 8), ("coarsen", 4),
+        ("solve", 2, 0.0), ("close", 2),
+        ("solve", 4, 0.0), ("prolong", 8, 4.0), ("close", 4),
+        ("solve", 8, 4.0 * 5 * 9 ** 3)]
+    assert [(lv["status"], lv["prolonged"]) for lv in info["levels"]] == [
+        ("NC_ERR_MAXIT", False), ("NC_OK", True)]
