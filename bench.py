@@ -213,10 +213,11 @@ def alu_probe(stream):
 def solve_block(workload, dev):
     """The full hot path once per precision, as one design iteration of an
     optimisation run (Sec. 3, Sec. 5.1): the state of the current design is
-    solved first (cold start, reported separately), the design takes one
-    synthetic optimiser step, then the timed part runs the warm-started Newton
-    state solve, the objective, the adjoint solve and the element sensitivities,
-    each to 1e-8 relative.  The objective is the mean patch temperature, so the
+    solved first (cold start, reported separately) and its adjoint, the design
+    takes one synthetic optimiser step, then the timed part runs the Newton
+    state solve warm-started from the previous state (to 1e-8), the objective,
+    the adjoint solve warm-started from the previous adjoint (to 1e-10) and the
+    element sensitivities.  The objective is the mean patch temperature, so the
     patch is heated by a flux (a prescribed patch temperature would make the
     objective constant).  The three modes share one context, which is freed on
     return; the FP64 state (or the mixed one) is returned for the J v step."""
@@ -236,9 +237,19 @@ def solve_block(workload, dev):
     solve["cold_state_mixed"] = {"s": round(time.perf_counter() - t0, 4),
                                  "newton_its": cinf["newton_its"],
                                  "lin_its": cinf["lin_its_total"], "status": cinf["status"]}
+    # the adjoint of the current design (mixed, from zero), the common warm start
+    # of the next design's adjoint in every mode
+    _, dphi0 = sprob.objective(x0)
+    t0 = time.perf_counter()
+    lam0, a0inf = sprob.adjoint_solve(x0, sg0, -dphi0, opts=nc.default_opts(mixed=1), check=False)
+    torch.cuda.synchronize()
+    solve["cold_adjoint_mixed"] = {"s": round(time.perf_counter() - t0, 4),
+                                   "lin_its": a0inf["lin_its_total"], "status": a0inf["status"]}
+    del dphi0
     xs = {}
     for mode, mixed, assembled in (("mixed", 1, 0), ("fp64", 0, 0), ("fp64_assembled", 0, 1)):
         opts = nc.default_opts(mixed=mixed, assembled=assembled, rtol_newton=1e-8, ramp_steps=3)
+        aopts = nc.default_opts(mixed=mixed, assembled=assembled, adjoint_start=1)
         # the first calls of a mode allocate its workspace and load its kernels:
         # one short untimed state and adjoint pass
         wopts = nc.default_opts(mixed=mixed, assembled=assembled, max_newton=1, max_lin=2)
@@ -255,8 +266,10 @@ def solve_block(workload, dev):
         torch.cuda.synchronize()
         ts = time.perf_counter() - t0
         phi, dphi = sprob.objective(xm)
+        lam = lam0.clone()
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        lam, ainf = sprob.adjoint_solve(xm, sg1, -dphi, opts=opts, check=False)
+        lam, ainf = sprob.adjoint_solve(xm, sg1, -dphi, lam=lam, opts=aopts, check=False)
         sens = sprob.sensitivity(xm, sg1, lam)
         torch.cuda.synchronize()
         ta = time.perf_counter() - t0
@@ -266,6 +279,8 @@ def solve_block(workload, dev):
                        "newton_its": inf["newton_its"], "lin_its": inf["lin_its_total"],
                        "state_status": inf["status"], "adjoint_lin_its": ainf["lin_its_total"],
                        "adjoint_status": ainf["status"],
+                       "adjoint_sweeps": ainf["newton_its"],
+                       "adjoint_rel_res_start": ainf["res_hist"][0] / max(ainf["res0"], 1e-300),
                        "rel_res_final": inf["res_final"] / max(inf["res0"], 1e-300),
                        "adjoint_rel_res_final": ainf["res_final"] / max(ainf["res0"], 1e-300),
                        "phi": phi}
@@ -291,8 +306,9 @@ def solve_block(workload, dev):
                           if synth.WORKLOADS[sw].get("bcs") == "quarter"
                           else "mean patch temperature, patch heated by a flux q = 1")
     solve["design_step"] = "gamma + 0.02 x box-filtered U[-1,1] in the design column (seed 77)"
+    solve["warm_starts"] = "state and adjoint from the previous design's (cold mixed solves)"
     x = (xb if solve["fp64"]["state_status"] == "NC_OK" else xa).clone()
-    del xs, xa, xb, xc, sa, sb, sc, sg0, sg1, x0
+    del xs, xa, xb, xc, sa, sb, sc, sg0, sg1, x0, lam0
     sprob.close()
     del sprob
     torch.cuda.empty_cache()

@@ -287,6 +287,9 @@ typedef struct {
                           solution error only through the conditioning of J, so the adjoint
                           is solved 100 times tighter than the state's default 1e-8: the
                           mixed and FP64 sensitivities then agree to about 1e-9 */
+  int adjoint_start;   /* nc_adjoint_solve's initial guess: 0 (default) lambda = 0; 1 the values
+                          in lambda_inout on entry (e.g. the previous design iteration's adjoint,
+                          as the state solve starts from the previous state, Sec. 5.1) */
 } nc_solve_opts;
 
 /* Per-solve report (Sec. 6.2 reports Newton and linear iteration counts). */
@@ -298,7 +301,8 @@ typedef struct {
 
 /* Fill opts with defaults (rtol_newton 1e-8, rtol_lin 1e-5, max_newton 30,
  * max_lin 200, restart 30, all levels, smooth_its 6, coarse_its 30, mixed 1,
- * ramp_steps 0, atol_newton 0, galerkin 0, assembled 0, rtol_adjoint 1e-10). */
+ * ramp_steps 0, atol_newton 0, galerkin 0, assembled 0, rtol_adjoint 1e-10,
+ * adjoint_start 0). */
 void nc_default_opts(nc_solve_opts* opts);
 
 /* Damped Newton (Sec. 5.1) on R(x, gamma) = 0 from x_inout (Dirichlet values
@@ -414,9 +418,12 @@ nc_status nc_prolong_state(nc_ctx* ctx, int level, const double* x_coarse, doubl
 /* Adjoint solve J(x, gamma)^T lambda = rhs (Sec. 3.2) by FGMRES + multigrid on the
  * transposed operators, inside FP64 iterative refinement until
  * ||rhs - J^T lambda|| <= rtol_adjoint ||rhs|| (max_newton refinement sweeps at
- * most).  All FP64 [5][Nn].  Synchronous. */
+ * most).  lambda_inout receives the solution; on entry it holds the initial
+ * guess when opts->adjoint_start = 1 and is not read otherwise (start from 0).
+ * info->res0 is ||rhs||, the refinement residuals go to info->res_hist (the
+ * first one that of the initial guess).  All FP64 [5][Nn].  Synchronous. */
 nc_status nc_adjoint_solve(nc_ctx* ctx, const double* x, const double* gamma,
-                           const double* rhs, double* lambda_out, const nc_solve_opts* opts,
+                           const double* rhs, double* lambda_inout, const nc_solve_opts* opts,
                            nc_solve_info* info, void* stream);
 
 #ifdef __cplusplus

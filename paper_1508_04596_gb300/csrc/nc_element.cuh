@@ -38,6 +38,8 @@ struct ElemConst {
   R inv_h;      // 1/h
   R wq;         // Gauss weight (h/2)^3
   R wh;         // wq / h: weight of the gradient-slot fluxes F1
+  R wc[2];      // wq * (1 -+ 1/sqrt 3)/2: the Gauss weight times the 1-D shape-function
+                // weights of the value-slot fluxes f0 (applied on the test side)
   R Pr, beta;   // Pr, Gr Pr^2
   R eg[3];      // unit gravity direction
   R beg[3];     // beta * eg
@@ -237,23 +239,23 @@ NC_HD void momentum_F1(const R G[3][3], R pw, const R u[3], const R a[3], const 
 }
 
 // ---------------------------------------------------------------------------- residual
-// Pointwise fluxes of the residual: w-scaled f0 and (w/h)-scaled F1.
+// Pointwise fluxes of the residual: f0 (the Gauss weight is applied on the test
+// side) and (w/h)-scaled F1.
 template <typename R>
 NC_HD void flux_residual(const QP<R>& q, const ElemCoef<R>& k, const ElemConst<R>& c, R f0[5],
                          R F1[5][3]) {
   R body[3], rM[3], rT;
   strong(q, k, c, body, rM, rT);
-  const R w = c.wq;
   R b[3];  // wh tau rM: the SUPG weight of the momentum rows and the PSPG flux
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     b[i] = k.wtau * rM[i];
-    f0[i] = w * body[i];
+    f0[i] = body[i];
     F1[3][i] = b[i];
   }
   momentum_F1<R, false>(q.G, c.wh * q.p, q.u, b, q.u, b, c, F1);
-  f0[3] = w * (q.G[0][0] + q.G[1][1] + q.G[2][2]);
-  f0[4] = w * rT;
+  f0[3] = q.G[0][0] + q.G[1][1] + q.G[2][2];
+  f0[4] = rT;
   const R trT = k.wtauT * rT;
 #pragma unroll
   for (int j = 0; j < 3; ++j) F1[4][j] = k.wK * q.gT[j] + q.u[j] * trT;
@@ -270,13 +272,13 @@ NC_HD void zero_out(R out[5][8]) {
 // ---------------------------------------------------------------------------- tangent
 // Directional derivative of the pointwise fluxes in the state direction d and,
 // with PARAM, the parameter directions (dalpha, dK); dtau, dtauT are the
-// derivatives of tau, tau_T along the same direction.  Returns w-scaled f0 and
-// (w/h)-scaled F1.  Without PARAM, dalpha and dK are not read (J v needs none).
+// derivatives of tau, tau_T along the same direction.  Returns f0 (the Gauss
+// weight is applied on the test side) and (w/h)-scaled F1.  Without PARAM,
+// dalpha and dK are not read (J v needs none).
 template <typename R, bool PARAM>
 NC_HD void flux_tangent_rm(const QP<R>& q, const R rM[3], R rT, const QP<R>& d,
                            const ElemCoef<R>& k, R dalpha, R dK, R dtau, R dtauT,
                            const ElemConst<R>& c, R f0[5], R F1[5][3]) {
-  const R w = c.wq;
   const R whdtau = c.wh * dtau;
   R a[3], b[3];
 #pragma unroll
@@ -286,7 +288,7 @@ NC_HD void flux_tangent_rm(const QP<R>& q, const R rM[3], R rT, const QP<R>& d,
              q.u[1] * d.G[i][1] + q.u[2] * d.G[i][2] + k.alpha * d.u[i] + c.beg[i] * d.T;
     if (PARAM) body += dalpha * q.u[i];
     const R drM = body + d.gp[i];
-    f0[i] = w * body;
+    f0[i] = body;
     // d(tau u_j rM_i) = u_j (dtau rM_i + tau drM_i) + d.u_j (tau rM_i), times wh
     a[i] = whdtau * rM[i] + k.wtau * drM;
     b[i] = k.wtau * rM[i];
@@ -295,8 +297,8 @@ NC_HD void flux_tangent_rm(const QP<R>& q, const R rM[3], R rT, const QP<R>& d,
   momentum_F1<R, true>(d.G, c.wh * d.p, q.u, a, d.u, b, c, F1);
   const R drT = d.u[0] * q.gT[0] + d.u[1] * q.gT[1] + d.u[2] * q.gT[2] + q.u[0] * d.gT[0] +
                 q.u[1] * d.gT[1] + q.u[2] * d.gT[2];
-  f0[3] = w * (d.G[0][0] + d.G[1][1] + d.G[2][2]);
-  f0[4] = w * drT;
+  f0[3] = d.G[0][0] + d.G[1][1] + d.G[2][2];
+  f0[4] = drT;
   const R aT = (c.wh * dtauT) * rT + k.wtauT * drT, bT = k.wtauT * rT;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
@@ -317,11 +319,11 @@ NC_HD void flux_tangent(const QP<R>& q, const QP<R>& d, const ElemCoef<R>& k, R 
 // ---------------------------------------------------------------------------- adjoint
 // Given the interpolated test field t (value and gradient per field at the
 // point), the cotangents of the point state, (dFlux/dq)^T (w t), returned as
-// f0 (value slots) and F1 (gradient slots, times 1/h) for the test-side
-// transpose, plus the cotangents of tau and tau_T accumulated WITHOUT the Gauss
-// weight w (the caller applies it once per element).  The weight is applied to
-// the 20 outputs rather than to the 20 seeds, and the symmetric viscous
-// cotangent is formed once per pair (i, j).
+// f0 (value slots, without the Gauss weight, which the test side applies) and F1
+// (gradient slots, times w/h) for the test-side transpose, plus the cotangents
+// of tau and tau_T accumulated WITHOUT the Gauss weight w (the caller applies it
+// once per element).  The weight is applied to the outputs rather than to the 20
+// seeds, and the symmetric viscous cotangent is formed once per pair (i, j).
 template <typename R>
 NC_HD void flux_adjoint_rm(const QP<R>& q, const R rM[3], R rT, const QP<R>& t,
                            const ElemCoef<R>& k, const ElemConst<R>& c, R f0[5], R F1[5][3],
@@ -372,18 +374,18 @@ NC_HD void flux_adjoint_rm(const QP<R>& q, const R rM[3], R rT, const QP<R>& t,
       Gb[i][j] += cb * q.u[j];
     }
   }
-  const R w = c.wq, wh = c.wh;
+  const R wh = c.wh;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    f0[i] = w * ub[i];
+    f0[i] = ub[i];
     F1[i][0] = wh * Gb[i][0];
     F1[i][1] = wh * Gb[i][1];
     F1[i][2] = wh * Gb[i][2];
     F1[3][i] = wh * rMb[i];
     F1[4][i] = wh * gTb[i];
   }
-  f0[3] = w * pb;
-  f0[4] = w * Tb;
+  f0[3] = pb;
+  f0[4] = Tb;
 }
 
 template <typename R>
@@ -408,7 +410,8 @@ NC_HD R point_sens(const QP<R>& q, const QP<R>& t, const ElemCoef<R>& k, R dalph
   }
   R f0[5], F1[5][3];
   flux_tangent<R, true>(q, zero, k, dalpha, dK, dtau, dtauT, c, f0, F1);
-  // F1 carries w/h; the test gradient t carries 1/h: multiply by h once
+  // f0 carries no weight: multiply by w once; F1 carries w/h and the test
+  // gradient t carries 1/h: multiply by h once
   const R h = R(1) / c.inv_h;
   R acc = f0[0] * t.u[0] + f0[1] * t.u[1] + f0[2] * t.u[2] + f0[3] * t.p + f0[4] * t.T;
   R acc1 = R(0);
@@ -416,7 +419,7 @@ NC_HD R point_sens(const QP<R>& q, const QP<R>& t, const ElemCoef<R>& k, R dalph
   for (int j = 0; j < 3; ++j)
     acc1 += F1[0][j] * t.G[0][j] + F1[1][j] * t.G[1][j] + F1[2][j] * t.G[2][j] +
             F1[3][j] * t.gp[j] + F1[4][j] * t.gT[j];
-  return acc + acc1 * h;
+  return c.wq * acc + acc1 * h;
 }
 
 // ---------------------------------------------------------------------------- linearisation cache
@@ -600,9 +603,13 @@ NC_HD void interp8(const R x[8], R inv_h, R val[8], R g[8][3]) {
 }
 
 // Transpose of interp8 (without the 1/h, which the caller folds into F1):
-// out[a] += sum_p [ N_a(p) f0[p] + dN_a/dxi_j(p) F1[p][j] ].
+// out[a] += sum_p [ w N_a(p) f0[p] + dN_a/dxi_j(p) F1[p][j] ], with the Gauss
+// weight w of the value slots applied here: wc = w (1 -+ 1/sqrt 3)/2.  The x stage
+// takes the two points of a pair to the two nodes: node 1 gets
+// wc0 f0[p0] + wc1 f0[p1] + F, node 0 gets wc1 f0[p0] + wc0 f0[p1] - F (the 1-D
+// weights of node 0 are those of node 1 mirrored), F the pair's x-gradient fluxes.
 template <typename R>
-NC_HD void test8(R out[8], const R f0[8], const R F1[8][3]) {
+NC_HD void test8(R out[8], const R f0[8], const R F1[8][3], const R wc[2]) {
   const R c[2] = {R(GW0), R(GW1)};
   R vyzb[2][2][2], dyb[2][2], dzyb[2][2];
 #pragma unroll
@@ -610,9 +617,9 @@ NC_HD void test8(R out[8], const R f0[8], const R F1[8][3]) {
 #pragma unroll
     for (int qy = 0; qy < 2; ++qy) {
       const int p0 = pt(0, qy, qz), p1 = pt(1, qy, qz);
-      const R dxb = c[0] * f0[p0] + c[1] * f0[p1] + (F1[p0][0] + F1[p1][0]);
-      vyzb[qz][qy][0] = f0[p0] + f0[p1] - dxb;
-      vyzb[qz][qy][1] = dxb;
+      const R F = F1[p0][0] + F1[p1][0];
+      vyzb[qz][qy][1] = wc[0] * f0[p0] + (wc[1] * f0[p1] + F);
+      vyzb[qz][qy][0] = wc[1] * f0[p0] + (wc[0] * f0[p1] - F);
     }
 #pragma unroll
   for (int qz = 0; qz < 2; ++qz) {
@@ -687,7 +694,7 @@ NC_HD void interp_all8(const R xe[5][8], R inv_h, QP<R> q[8]) {
 }
 
 template <typename R>
-NC_HD void test_all8(R out[5][8], const R f0[8][5], const R F1[8][5][3]) {
+NC_HD void test_all8(R out[5][8], const R f0[8][5], const R F1[8][5][3], const R wc[2]) {
 #pragma unroll
   for (int f = 0; f < 5; ++f) {
     R a[8], b[8][3];
@@ -698,7 +705,7 @@ NC_HD void test_all8(R out[5][8], const R f0[8][5], const R F1[8][5][3]) {
       b[p][1] = F1[p][f][1];
       b[p][2] = F1[p][f][2];
     }
-    test8<R>(out[f], a, b);
+    test8<R>(out[f], a, b, wc);
   }
 }
 
@@ -712,7 +719,7 @@ NC_HD void elem_residual(const R xe[5][8], R gam, R s, const ElemConst<R>& c, R 
 #pragma unroll
   for (int p = 0; p < 8; ++p) flux_residual(q[p], k, c, f0[p], F1[p]);
   zero_out(out);
-  test_all8<R>(out, f0, F1);
+  test_all8<R>(out, f0, F1, c.wc);
 }
 
 template <typename R>
@@ -735,7 +742,7 @@ NC_HD void elem_jvp(const R xe[5][8], const R ve[5][8], R gam, R s, const ElemCo
   for (int p = 0; p < 8; ++p)
     flux_tangent<R, false>(q[p], d[p], k, R(0), R(0), dtau, dtauT, c, f0[p], F1[p]);
   zero_out(out);
-  test_all8<R>(out, f0, F1);
+  test_all8<R>(out, f0, F1, c.wc);
 }
 
 template <typename R>
@@ -751,7 +758,7 @@ NC_HD void elem_jtvp(const R xe[5][8], const R we[5][8], R gam, R s, const ElemC
 #pragma unroll
   for (int p = 0; p < 8; ++p) flux_adjoint(q[p], t[p], k, c, f0[p], F1[p], tb, tbT);
   zero_out(out);
-  test_all8<R>(out, f0, F1);
+  test_all8<R>(out, f0, F1, c.wc);
   const R gsum = -(k.tau * k.tau * k.tau * tb + k.tauT * k.tauT * k.tauT * tbT) * (c.wq * c.inv16h2);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -828,7 +835,7 @@ NC_HD void elem_jvp_lin(const R* cache, long long stride, const R ue[3][8], cons
                                 c, f0[2 * P + sx], F1[2 * P + sx]);
   }
   zero_out(out);
-  test_all8<R>(out, f0, F1);
+  test_all8<R>(out, f0, F1, c.wc);
 }
 
 template <typename R>
@@ -850,7 +857,7 @@ NC_HD void elem_jtvp_lin(const R* cache, long long stride, const R ue[3][8], con
                       tb, tbT);
   }
   zero_out(out);
-  test_all8<R>(out, f0, F1);
+  test_all8<R>(out, f0, F1, c.wc);
   const R gsum = -(k.tau * k.tau * k.tau * tb + k.tauT * k.tauT * k.tauT * tbT) * (c.wq * c.inv16h2);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -868,7 +875,6 @@ template <typename R, int G>
 NC_HD void flux_column(const QP<R>& q, const R rM[3], R rT, R phi, const R psi[3],
                        const ElemCoef<R>& k, R whdtau, R whdtauT, const ElemConst<R>& c, R f0[5],
                        R F1[5][3]) {
-  const R w = c.wq;
   if (G < 3) {
     const R upsi = q.u[0] * psi[0] + q.u[1] * psi[1] + q.u[2] * psi[2];
     R a[3], b[3];
@@ -876,7 +882,7 @@ NC_HD void flux_column(const QP<R>& q, const R rM[3], R rT, R phi, const R psi[3
     for (int i = 0; i < 3; ++i) {
       R body = phi * q.G[i][G];  // d.u . grad u_i
       if (i == G) body += upsi + k.alpha * phi;
-      f0[i] = w * body;
+      f0[i] = body;
       a[i] = whdtau * rM[i] + k.wtau * body;
       b[i] = k.wtau * rM[i];
       F1[3][i] = a[i];
@@ -893,8 +899,8 @@ NC_HD void flux_column(const QP<R>& q, const R rM[3], R rT, R phi, const R psi[3
         F1[i][j] = t;
       }
     const R drT = phi * q.gT[G];
-    f0[3] = w * psi[G];
-    f0[4] = w * drT;
+    f0[3] = psi[G];
+    f0[4] = drT;
     const R aT = whdtauT * rT + k.wtauT * drT, bT = k.wtauT * rT;
 #pragma unroll
     for (int j = 0; j < 3; ++j) F1[4][j] = j == G ? q.u[j] * aT + phi * bT : q.u[j] * aT;
@@ -919,7 +925,7 @@ NC_HD void flux_column(const QP<R>& q, const R rM[3], R rT, R phi, const R psi[3
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const R body = c.beg[i] * phi;
-      f0[i] = w * body;
+      f0[i] = body;
       a[i] = k.wtau * body;
       F1[3][i] = a[i];
     }
@@ -929,7 +935,7 @@ NC_HD void flux_column(const QP<R>& q, const R rM[3], R rT, R phi, const R psi[3
       for (int j = 0; j < 3; ++j) F1[i][j] = q.u[j] * a[i];
     const R drT = q.u[0] * psi[0] + q.u[1] * psi[1] + q.u[2] * psi[2];
     f0[3] = R(0);
-    f0[4] = w * drT;
+    f0[4] = drT;
     const R aT = k.wtauT * drT;
 #pragma unroll
     for (int j = 0; j < 3; ++j) F1[4][j] = k.wK * psi[j] + q.u[j] * aT;
@@ -984,7 +990,7 @@ NC_HD void elem_column_lin(const R* cache, long long stride, R ub, int b, R gam,
       b0[p][1] = F1[p][f][1];
       b0[p][2] = F1[p][f][2];
     }
-    test8<R>(out[f], a0, b0);
+    test8<R>(out[f], a0, b0, c.wc);
   }
 }
 
@@ -995,6 +1001,8 @@ NC_HD ElemConst<R> make_const(double h, double Gr, double Pr, double amax, doubl
   c.inv_h = R(1.0 / h);
   c.wq = R((h / 2) * (h / 2) * (h / 2));
   c.wh = R((h / 2) * (h / 2) * (h / 2) / h);
+  c.wc[0] = R((h / 2) * (h / 2) * (h / 2) * GW0);
+  c.wc[1] = R((h / 2) * (h / 2) * (h / 2) * GW1);
   c.Pr = R(Pr);
   c.beta = R(Gr * Pr * Pr);
   c.eg[0] = R(eg[0]);

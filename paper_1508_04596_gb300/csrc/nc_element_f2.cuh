@@ -206,9 +206,11 @@ NC_HD void interp_all_f2(const float xe[5][8], float inv_h, const Const2& K, QP2
 
 // ------------------------------------------------------------------ test side
 // Transpose of interp8_f2 (without the 1/h, folded into F1): out[a] +=
-// sum_p [N_a(p) f0[p] + dN_a/dxi_j(p) F1[p][j]], with f0, F1 as point pairs and
-// out as node pairs out[ja + 2 ka] = (out[a], out[a + 1]).
-NC_HD void test8_f2(f2 out[4], const f2 f0[4], const f2 F1[4][3], const Const2& K) {
+// sum_p [w N_a(p) f0[p] + dN_a/dxi_j(p) F1[p][j]] (test8, with the value slots'
+// Gauss weight applied here, wc = w (1 -+ 1/sqrt 3)/2), with f0, F1 as point
+// pairs and out as node pairs out[ja + 2 ka] = (out[a], out[a + 1]).
+NC_HD void test8_f2(f2 out[4], const f2 f0[4], const f2 F1[4][3], const float wc[2],
+                    const Const2& K) {
   const float c[2] = {float(GW0), float(GW1)};
   // x stage: point pairs -> node pairs
   f2 VYZB[2][2];
@@ -217,9 +219,9 @@ NC_HD void test8_f2(f2 out[4], const f2 f0[4], const f2 F1[4][3], const Const2& 
 #pragma unroll
     for (int qy = 0; qy < 2; ++qy) {
       const int P = qy + 2 * qz;
-      const f2 f = f0[P], F = F1[P][0];
-      const float dxb = c[0] * f.x + c[1] * f.y + (F.x + F.y);
-      VYZB[qz][qy] = mk2(f.x + f.y - dxb, dxb);
+      const f2 f = f0[P], Fp = F1[P][0];
+      const float F = Fp.x + Fp.y;
+      VYZB[qz][qy] = mk2(wc[1] * f.x + (wc[0] * f.y - F), wc[0] * f.x + (wc[1] * f.y + F));
     }
   f2 DYB[2];
 #pragma unroll
@@ -255,7 +257,7 @@ NC_HD void test8_f2(f2 out[4], const f2 f0[4], const f2 F1[4][3], const Const2& 
 }
 
 NC_HD void test_all_f2(float out[5][8], const f2 f0[4][5], const f2 F1[4][5][3],
-                       const Const2& K) {
+                       const float wc[2], const Const2& K) {
 #pragma unroll
   for (int f = 0; f < 5; ++f) {
     f2 a[4], b[4][3], o[4];
@@ -267,7 +269,7 @@ NC_HD void test_all_f2(float out[5][8], const f2 f0[4][5], const f2 F1[4][5][3],
       b[P][2] = F1[P][f][2];
       o[P] = mk2(0.0f, 0.0f);
     }
-    test8_f2(o, a, b, K);
+    test8_f2(o, a, b, wc, K);
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
       out[f][2 * n] = o[n].x;
@@ -290,7 +292,8 @@ NC_HD void strong_f2(const QP2& q, const Coef2& k, const Const2& K, f2 body[3], 
 }
 
 // Tangent fluxes of a point pair in the state direction d (flux_tangent_rm
-// without the parameter directions), w-scaled f0 and (w/h)-scaled F1.
+// without the parameter directions): f0 without the Gauss weight (applied on the
+// test side) and (w/h)-scaled F1.
 NC_HD void flux_tangent_f2(const QP2& q, const f2 rM[3], f2 rT, const QP2& d, const Coef2& k,
                            f2 whdtau, f2 whdtauT, const Const2& K, f2 f0[5], f2 F1[5][3]) {
   f2 a[3], b[3];
@@ -305,7 +308,7 @@ NC_HD void flux_tangent_f2(const QP2& q, const f2 rM[3], f2 rT, const QP2& d, co
     body = fma2(k.alpha, d.u[i], body);
     body = fma2(K.beg[i], d.T, body);
     const f2 drM = add2(body, d.gp[i]);
-    f0[i] = mul2(K.wq, body);
+    f0[i] = body;
     a[i] = fma2(whdtau, rM[i], mul2(k.wtau, drM));
     b[i] = mul2(k.wtau, rM[i]);
     F1[3][i] = a[i];
@@ -328,15 +331,16 @@ NC_HD void flux_tangent_f2(const QP2& q, const f2 rM[3], f2 rT, const QP2& d, co
   drT = fma2(q.u[0], d.gT[0], drT);
   drT = fma2(q.u[1], d.gT[1], drT);
   drT = fma2(q.u[2], d.gT[2], drT);
-  f0[3] = mul2(K.wq, add2(add2(d.G[0][0], d.G[1][1]), d.G[2][2]));
-  f0[4] = mul2(K.wq, drT);
+  f0[3] = add2(add2(d.G[0][0], d.G[1][1]), d.G[2][2]);
+  f0[4] = drT;
   const f2 aT = fma2(whdtauT, rT, mul2(k.wtauT, drT)), bT = mul2(k.wtauT, rT);
 #pragma unroll
   for (int j = 0; j < 3; ++j) F1[4][j] = fma2(d.u[j], bT, fma2(q.u[j], aT, mul2(k.wK, d.gT[j])));
 }
 
 // Cotangent fluxes of a point pair for the test field t (flux_adjoint_rm):
-// f0 (value slots, w-scaled) and F1 (gradient slots, (w/h)-scaled); the
+// f0 (value slots, without the Gauss weight) and F1 (gradient slots,
+// (w/h)-scaled); the
 // cotangents of tau and tau_T are accumulated per lane, without the weight.
 NC_HD void flux_adjoint_f2(const QP2& q, const f2 rM[3], f2 rT, const QP2& t, const Coef2& k,
                            const Const2& K, f2 f0[5], f2 F1[5][3], f2& tau_bar, f2& tauT_bar) {
@@ -386,15 +390,15 @@ NC_HD void flux_adjoint_f2(const QP2& q, const f2 rM[3], f2 rT, const QP2& t, co
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    f0[i] = mul2(K.wq, ub[i]);
+    f0[i] = ub[i];
     F1[i][0] = mul2(K.wh, Gb[i][0]);
     F1[i][1] = mul2(K.wh, Gb[i][1]);
     F1[i][2] = mul2(K.wh, Gb[i][2]);
     F1[3][i] = mul2(K.wh, rMb[i]);
     F1[4][i] = mul2(K.wh, gTb[i]);
   }
-  f0[3] = mul2(K.wq, pb);
-  f0[4] = mul2(K.wq, Tb);
+  f0[3] = pb;
+  f0[4] = Tb;
 }
 
 // ------------------------------------------------------------------ element products
@@ -423,7 +427,7 @@ NC_HD void elem_jvp_f2(const float xe[5][8], const float ve[5][8], float gam, fl
     strong_f2(q[P], k, K, body, rM, rT);
     flux_tangent_f2(q[P], rM, rT, d[P], k, whdtau, whdtauT, K, f0[P], F1[P]);
   }
-  test_all_f2(out, f0, F1, K);
+  test_all_f2(out, f0, F1, c.wc, K);
 }
 
 // J^T w of one element (elem_jtvp<float> on point pairs).
@@ -444,7 +448,7 @@ NC_HD void elem_jtvp_f2(const float xe[5][8], const float we[5][8], float gam, f
     strong_f2(q[P], k, K, body, rM, rT);
     flux_adjoint_f2(q[P], rM, rT, t[P], k, K, f0[P], F1[P], tb, tbT);
   }
-  test_all_f2(out, f0, F1, K);
+  test_all_f2(out, f0, F1, c.wc, K);
   const float tbs = tb.x + tb.y, tbTs = tbT.x + tbT.y;
   const float gsum = -(ks.tau * ks.tau * ks.tau * tbs + ks.tauT * ks.tauT * ks.tauT * tbTs) *
                      (c.wq * c.inv16h2);

@@ -542,7 +542,8 @@ nc_status prepare(nc_ctx* ctx, const nc_solve_opts& o, int nlev, bool mixed) {
   if (o.restart < 1 || o.restart > MAX_RESTART || o.smooth_its < 1 ||
       o.smooth_its > MAX_RESTART || o.coarse_its < 1 || o.coarse_its > MAX_RESTART ||
       o.max_lin < 1 || o.max_newton < 0 || !(o.rtol_lin > 0.0) || !(o.rtol_newton >= 0.0) ||
-      !(o.atol_newton >= 0.0) || !(o.rtol_adjoint >= 0.0))
+      !(o.atol_newton >= 0.0) || !(o.rtol_adjoint >= 0.0) || o.adjoint_start < 0 ||
+      o.adjoint_start > 1)
     return set_err(ctx, NC_ERR_ARG, "invalid solver options");
   if (ctx->kry.m < o.restart) {
     cudaFree(ctx->kry.V);
@@ -705,6 +706,7 @@ void nc_default_opts(nc_solve_opts* o) {
   o->galerkin = 0;
   o->assembled = 0;
   o->rtol_adjoint = 1e-10;
+  o->adjoint_start = 0;
 }
 
 nc_status nc_newton_solve(nc_ctx* ctx, const double* gam, double* x, const nc_solve_opts* opts,
@@ -865,15 +867,21 @@ nc_status nc_adjoint_solve(nc_ctx* ctx, const double* x, const double* gam, cons
     double* r = ctx->tmp64[0];
     double* dl = ctx->tmp64[1];
     double* t = ctx->tmp64[2];
-    vzero(n, lam, s);
-    vcopy(n, rhs, r, s);
     double nb;
     st = norm2(ctx, n, rhs, &nb, s);
     info.res0 = nb;
-    info.res_hist[0] = nb;
+    double nr = nb;
+    if (o.adjoint_start) {  // warm start: the FP64 residual of the given lambda
+      op_jtvp<double>(L.d, L.c64, x, gam, ctx->src64, lam, t, ctx->Y, s);
+      vwaxpy(n, rhs, -1.0, (const double*)t, r, s);
+      if (st == NC_OK) st = norm2(ctx, n, r, &nr, s);
+    } else {
+      vzero(n, lam, s);
+      vcopy(n, rhs, r, s);
+    }
+    info.res_hist[0] = nr;
     const LinSolve ls{true, mixed, nlev};
     int k = 0;
-    double nr = nb;
     // the state and the design do not change during the refinement: one
     // linearisation of every level serves all sweeps
     bool linearized = false;

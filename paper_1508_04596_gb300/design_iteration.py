@@ -2,12 +2,15 @@
 
     python -m paper_1508_04596_gb300.design_iteration WORKLOAD [--fp64] [--no-adjoint] [--galerkin]
                                                       [--assembled] [--restart M] [--sequence]
+                                                      [--cold-adjoint]
 
-Solves the state of the workload's design from a cold start, takes one
-synthetic optimiser step of the design (``synth.design_step``), then runs the
-warm-started Newton state solve, the objective, the adjoint solve and the
-element sensitivities (Sec. 3.2, Sec. 5) inside an NVTX range named "warm", so
-that a profiler can be restricted to it (``ncu --nvtx --nvtx-include warm/``).
+Solves the state and the adjoint of the workload's design from a cold start,
+takes one synthetic optimiser step of the design (``synth.design_step``), then
+runs the Newton state solve warm-started from the previous state, the
+objective, the adjoint solve warm-started from the previous adjoint (from zero
+with --cold-adjoint) and the element sensitivities (Sec. 3.2, Sec. 5) inside an
+NVTX range named "warm", so that a profiler can be restricted to it
+(``ncu --nvtx --nvtx-include warm/``).
 Prints the iteration counts and wall times of the warm part.  With --galerkin the
 warm solves use Galerkin coarse operators (P^T A P) instead of rediscretised ones.
 """
@@ -31,6 +34,8 @@ def main(argv=None):
     ap.add_argument("--restart", type=int, default=30, help="FGMRES restart (memory: 2 vectors each)")
     ap.add_argument("--sequence", action="store_true",
                     help="cold start by grid sequencing (solve the coarser grids first)")
+    ap.add_argument("--cold-adjoint", action="store_true",
+                    help="start the warm iteration's adjoint from zero, not the previous adjoint")
     a = ap.parse_args(argv)
     mixed = 0 if a.fp64 else 1
     prob = nc.Problem.from_workload(a.workload, patch="flux")
@@ -50,6 +55,12 @@ def main(argv=None):
     cold = {"cold_state_s": time.perf_counter() - t0, "cold_newton_its": cinf["newton_its"],
             "cold_lin_its": cinf["lin_its_total"], "cold_levels": cinf.get("levels"),
             "cold_res_hist": cinf["res_hist"]}
+    lam = None
+    if not a.no_adjoint and not a.cold_adjoint:  # the previous design's adjoint
+        _, d0 = prob.objective(x)
+        lam, a0 = prob.adjoint_solve(x, g0, -d0, opts=nc.default_opts(mixed=1, restart=a.restart))
+        cold["cold_adjoint_lin_its"] = a0["lin_its_total"]
+        del d0
     # load the kernels and allocate the workspace of this precision (untimed)
     gal = 1 if a.galerkin else 0
     asm = 1 if a.assembled else 0
@@ -73,7 +84,9 @@ def main(argv=None):
     if not a.no_adjoint:
         t0 = time.perf_counter()
         phi, dphi = prob.objective(x)
-        lam, ainf = prob.adjoint_solve(x, g1, -dphi, opts=nc.default_opts(**kw), check=False)
+        lam, ainf = prob.adjoint_solve(x, g1, -dphi, lam=lam,
+                                       opts=nc.default_opts(adjoint_start=int(lam is not None), **kw),
+                                       check=False)
         prob.sensitivity(x, g1, lam)
         torch.cuda.synchronize()
         out.update(adjoint_plus_sens_s=time.perf_counter() - t0, phi=phi,

@@ -51,7 +51,8 @@ class SolveOpts(ctypes.Structure):
                 ("smooth_its", ctypes.c_int), ("coarse_its", ctypes.c_int),
                 ("mixed", ctypes.c_int), ("ramp_steps", ctypes.c_int),
                 ("atol_newton", ctypes.c_double), ("galerkin", ctypes.c_int),
-                ("assembled", ctypes.c_int), ("rtol_adjoint", ctypes.c_double)]
+                ("assembled", ctypes.c_int), ("rtol_adjoint", ctypes.c_double),
+                ("adjoint_start", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -553,8 +554,13 @@ class Problem:
         return x, info.as_dict()
 
     def adjoint_solve(self, x, gam, rhs, lam=None, opts=None, stream=None, check=True):
+        """J^T lam = rhs.  lam (optional) receives the solution; with
+        opts.adjoint_start = 1 its values on entry are the initial guess."""
         opts = default_opts() if opts is None else opts
-        lam = torch.empty_like(x) if lam is None else lam
+        if lam is None:
+            if opts.adjoint_start:
+                raise ValueError("adjoint_start = 1 needs the initial guess in lam")
+            lam = torch.empty_like(x)
         info = SolveInfo()
         st = lib.nc_adjoint_solve(self.ctx, self._vec(x, torch.float64, self.ndof, "x"),
                                   self._vec(gam, torch.float64, self.E, "gamma"),

@@ -76,10 +76,11 @@ class Optimizer:
         self.prob = None
         self.step = -1
         self.x = None
+        self.lam = None  # the last adjoint: the next adjoint solve's initial guess
         self.f0_scale = None
         self.schedule = None  # (iters, steps) of the run's continuation schedule
 
-    _TENSORS = ("rho", "xold1", "xold2", "low", "upp", "x")
+    _TENSORS = ("rho", "xold1", "xold2", "low", "upp", "x", "lam")
 
     def state_dict(self):
         """Everything a resumed run needs, as host tensors and plain values."""
@@ -135,8 +136,10 @@ class Optimizer:
         sopts = nc.default_opts(mixed=self.mixed, rtol_newton=self.state_rtol, ramp_steps=3)
         _, sinf = p.newton_solve(gam, self.x, sopts, check=False)
         phi, dphi = p.objective(self.x)
-        aopts = nc.default_opts(mixed=self.mixed, rtol_adjoint=self.adjoint_rtol)
-        lam, ainf = p.adjoint_solve(self.x, gam, -dphi, opts=aopts, check=False)
+        aopts = nc.default_opts(mixed=self.mixed, rtol_adjoint=self.adjoint_rtol,
+                                adjoint_start=int(self.lam is not None))
+        lam, ainf = p.adjoint_solve(self.x, gam, -dphi, lam=self.lam, opts=aopts, check=False)
+        self.lam = lam
         sens = p.sensitivity(self.x, gam, lam)
         # chain rule of the filter (symmetric) on the design variables only
         dfdrho = p.filter(p.design_map(sens, self.active, out=sens))

@@ -52,7 +52,7 @@ def test_default_opts(lib):
     assert (o.galerkin, o.assembled, o.rtol_adjoint) == (0, 0, 1e-10)
 
 
-@pytest.mark.parametrize("struct,fill,last", [("SolveOpts", "nc_default_opts", "rtol_adjoint"),
+@pytest.mark.parametrize("struct,fill,last", [("SolveOpts", "nc_default_opts", "adjoint_start"),
                                              ("MmaOpts", "nc_default_mma_opts", "df0_scale")])
 def test_option_structs_match_the_header(lib, struct, fill, last):
     """The ctypes mirrors of the option structs have the C layout: the library's

@@ -269,3 +269,37 @@ def test_grid_sequencing_cold_start(nc):
     assert float(torch.linalg.norm(va - vb) / torch.linalg.norm(va)) <= 1e-8
     assert qb.objective(xb)[0] == pytest.approx(qa.objective(xa)[0], rel=1e-10)
     assert ib["lin_its_total"] <= ia["lin_its_total"], (ia, ib)
+
+
+def test_adjoint_warm_start(nc):
+    """adjoint_start = 1 (Sec. 3.2 adjoint, started like the state solve from the
+    previous design iteration's solution): from the converged adjoint the solve
+    does no sweep and returns it unchanged; from the adjoint of a neighbouring
+    design it reaches the cold solve's solution (1e-8) with fewer FGMRES
+    iterations; adjoint_start without an initial guess is refused."""
+    n = 16
+    p = nc.make_params(n, n, n, 1.0 / n, 1e4, 0.71, **synth.MATERIAL)
+    prob = nc.Problem(p, nc.cavity_bcs(nc.PATCH_FLUX, 1.0))
+    g0 = synth.smoothed_random(n, n, n, 1.0 / n, 21)
+    g1 = synth.design_step({"nx": n, "ny": n, "nz": n, "h": 1.0 / n}, g0, 22)
+    rel = lambda a, b: (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item()
+    sols = []
+    for g in (g0, g1):
+        x = torch.zeros(prob.ndof, dtype=torch.float64, device="cuda")
+        prob.newton_solve(dev(g), x, nc.default_opts(rtol_newton=1e-10))
+        _, dphi = prob.objective(x)
+        lam, info = prob.adjoint_solve(x, dev(g), -dphi)
+        sols.append((x, dphi, lam, info))
+    x1, d1, lam1, cold = sols[1]
+    again, info = prob.adjoint_solve(x1, dev(g1), -d1, lam=lam1.clone(),
+                                     opts=nc.default_opts(adjoint_start=1))
+    assert info["newton_its"] == 0 and info["lin_its_total"] == 0
+    assert torch.equal(again, lam1)
+    warm, info = prob.adjoint_solve(x1, dev(g1), -d1, lam=sols[0][2].clone(),
+                                    opts=nc.default_opts(adjoint_start=1))
+    assert info["status"] == "NC_OK" and info["res_final"] <= 1e-10 * info["res0"]
+    assert info["res_hist"][0] < info["res0"]  # the guess is better than zero
+    assert rel(warm, lam1) <= 1e-8
+    assert info["lin_its_total"] < cold["lin_its_total"], (info, cold)
+    with pytest.raises(ValueError):
+        prob.adjoint_solve(x1, dev(g1), -d1, opts=nc.default_opts(adjoint_start=1))
