@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--solve-workload", default=None,
                     help="workload of the state/adjoint design-iteration timing (default: --workload)")
+    ap.add_argument("--solve-only", action="store_true",
+                    help="only the design-iteration solve block of --workload, printed as JSON")
     ap.add_argument("--jv-only", action="store_true",
                     help="only the timed J v step (profiling runs: no end-to-end, operator, "
                          "assembled or vector measurements)")
@@ -228,15 +230,20 @@ def solve_block(workload, dev):
     sprob = nc.Problem.from_workload(sw, patch="flux")
     sg0 = torch.tensor(synth.design(sw), dtype=torch.float64, device=dev)
     sg1 = torch.tensor(synth.design_step(sw, synth.design(sw), 77), dtype=torch.float64, device=dev)
-    # cold start of the current design (mixed), the common warm start of all modes
+    # cold start of the current design (mixed, grid sequencing: the coarser grids of
+    # the multigrid hierarchy solved first), the common warm start of all modes
     x0 = torch.zeros(sprob.ndof, dtype=torch.float64, device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    _, cinf = sprob.newton_solve(sg0, x0, nc.default_opts(mixed=1, ramp_steps=3), check=False)
+    _, cinf = sprob.newton_solve_sequenced(sg0, x0, nc.default_opts(mixed=1, ramp_steps=3),
+                                           check=False)
     torch.cuda.synchronize()
     solve["cold_state_mixed"] = {"s": round(time.perf_counter() - t0, 4),
+                                 "method": "grid sequencing (coarsest grid first), load ramping",
                                  "newton_its": cinf["newton_its"],
-                                 "lin_its": cinf["lin_its_total"], "status": cinf["status"]}
+                                 "lin_its": cinf["lin_its_total"], "status": cinf["status"],
+                                 "coarser_grids": [[lv["dims"], lv["newton_its"], lv["lin_its"]]
+                                                   for lv in cinf.get("levels", [])]}
     # the adjoint of the current design (mixed, from zero), the common warm start
     # of the next design's adjoint in every mode
     _, dphi0 = sprob.objective(x0)
@@ -742,6 +749,11 @@ def main():
         prob = nc.Problem(nc.make_params(2, 2, 2, 0.5, 1e3, 0.71), nc.cavity_bcs())
         only = None if args.vectors_only == "both" else args.vectors_only
         print(json.dumps(hbm_kernels(prob, torch.cuda.current_stream(), only=only)))
+        return
+    if args.solve_only:
+        import torch
+        solve, _ = solve_block(args.workload, torch.device("cuda"))
+        print(json.dumps(solve))
         return
     rank, world = dist_init(args)
     line = run_reference(args, rank, world) if args.impl == "reference" else run_ours(args, rank, world)

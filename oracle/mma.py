@@ -30,6 +30,19 @@ S0, INCR, DECR = 0.5, 1.2, 0.7
 RAA0 = 1e-5
 
 
+def volume_constraint(gam, active, vf, h=1.0):
+    """The volume constraint of Sec. 3.2 normalised by the allowed volume:
+    g = int_{Omega_d} (1 - gamma) dV / (v_f |Omega_d|) - 1  (<= 0 when satisfied),
+    gamma element-constant on cubes of edge h, Omega_d the active (design)
+    elements (all when active is None).  Returns g and dg/dgamma_e (0 on
+    inactive elements)."""
+    gam = np.asarray(gam, dtype=float)
+    act = np.ones(gam.shape, bool) if active is None else np.asarray(active, bool)
+    vol_d = h ** 3 * act.sum()
+    g = h ** 3 * np.sum(1.0 - gam[act]) / (vf * vol_d) - 1.0
+    return g, np.where(act, -h ** 3 / (vf * vol_d), 0.0)
+
+
 def asymptotes(k, x, xold1, xold2, low, upp, xmin, xmax):
     """Asymptotes for iteration k (0-based) from the two previous iterates and
     the previous asymptotes."""

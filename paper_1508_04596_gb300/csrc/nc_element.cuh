@@ -603,7 +603,8 @@ NC_HD void interp8(const R x[8], R inv_h, R val[8], R g[8][3]) {
 }
 
 // Transpose of interp8 (without the 1/h, which the caller folds into F1):
-// out[a] += sum_p [ w N_a(p) f0[p] + dN_a/dxi_j(p) F1[p][j] ], with the Gauss
+// out[a] = sum_p [ w N_a(p) f0[p] + dN_a/dxi_j(p) F1[p][j] ] (written, not added:
+// a sum onto zeros would cost an addition per row), with the Gauss
 // weight w of the value slots applied here: wc = w (1 -+ 1/sqrt 3)/2.  The x stage
 // takes the two points of a pair to the two nodes: node 1 gets
 // wc0 f0[p0] + wc1 f0[p1] + F, node 0 gets wc1 f0[p0] + wc0 f0[p1] - F (the 1-D
@@ -656,8 +657,8 @@ NC_HD void test8(R out[8], const R f0[8], const R F1[8][3], const R wc[2]) {
 #pragma unroll
   for (int col = 0; col < 4; ++col) {
     const R d = dzb[col] + c[0] * vzb[0][col] + c[1] * vzb[1][col];
-    out[col] += vzb[0][col] + vzb[1][col] - d;
-    out[col + 4] += d;
+    out[col] = vzb[0][col] + vzb[1][col] - d;
+    out[col + 4] = d;
   }
 }
 
@@ -718,7 +719,6 @@ NC_HD void elem_residual(const R xe[5][8], R gam, R s, const ElemConst<R>& c, R 
   R f0[8][5], F1[8][5][3];
 #pragma unroll
   for (int p = 0; p < 8; ++p) flux_residual(q[p], k, c, f0[p], F1[p]);
-  zero_out(out);
   test_all8<R>(out, f0, F1, c.wc);
 }
 
@@ -741,7 +741,6 @@ NC_HD void elem_jvp(const R xe[5][8], const R ve[5][8], R gam, R s, const ElemCo
 #pragma unroll
   for (int p = 0; p < 8; ++p)
     flux_tangent<R, false>(q[p], d[p], k, R(0), R(0), dtau, dtauT, c, f0[p], F1[p]);
-  zero_out(out);
   test_all8<R>(out, f0, F1, c.wc);
 }
 
@@ -757,7 +756,6 @@ NC_HD void elem_jtvp(const R xe[5][8], const R we[5][8], R gam, R s, const ElemC
   R tb = R(0), tbT = R(0);
 #pragma unroll
   for (int p = 0; p < 8; ++p) flux_adjoint(q[p], t[p], k, c, f0[p], F1[p], tb, tbT);
-  zero_out(out);
   test_all8<R>(out, f0, F1, c.wc);
   const R gsum = -(k.tau * k.tau * k.tau * tb + k.tauT * k.tauT * k.tauT * tbT) * (c.wq * c.inv16h2);
 #pragma unroll
@@ -834,7 +832,6 @@ NC_HD void elem_jvp_lin(const R* cache, long long stride, const R ue[3][8], cons
       flux_tangent_rm<R, false>(q[sx], rM[sx], rT[sx], d[2 * P + sx], k, R(0), R(0), dtau, dtauT,
                                 c, f0[2 * P + sx], F1[2 * P + sx]);
   }
-  zero_out(out);
   test_all8<R>(out, f0, F1, c.wc);
 }
 
@@ -856,7 +853,6 @@ NC_HD void elem_jtvp_lin(const R* cache, long long stride, const R ue[3][8], con
       flux_adjoint_rm(q[sx], rM[sx], rT[sx], t[2 * P + sx], k, c, f0[2 * P + sx], F1[2 * P + sx],
                       tb, tbT);
   }
-  zero_out(out);
   test_all8<R>(out, f0, F1, c.wc);
   const R gsum = -(k.tau * k.tau * k.tau * tb + k.tauT * k.tauT * k.tauT * tbT) * (c.wq * c.inv16h2);
 #pragma unroll
@@ -978,10 +974,13 @@ NC_HD void elem_column_lin(const R* cache, long long stride, R ub, int b, R gam,
                         F1[p]);
     }
   }
-  zero_out(out);
 #pragma unroll
   for (int f = 0; f < 5; ++f) {
-    if (G == 3 && f == 4) continue;  // the energy rows do not see the pressure
+    if (G == 3 && f == 4) {  // the energy rows do not see the pressure
+#pragma unroll
+      for (int a = 0; a < 8; ++a) out[f][a] = R(0);
+      continue;
+    }
     R a0[8], b0[8][3];
 #pragma unroll
     for (int p = 0; p < 8; ++p) {

@@ -205,7 +205,7 @@ NC_HD void interp_all_f2(const float xe[5][8], float inv_h, const Const2& K, QP2
 }
 
 // ------------------------------------------------------------------ test side
-// Transpose of interp8_f2 (without the 1/h, folded into F1): out[a] +=
+// Transpose of interp8_f2 (without the 1/h, folded into F1): out[a] =
 // sum_p [w N_a(p) f0[p] + dN_a/dxi_j(p) F1[p][j]] (test8, with the value slots'
 // Gauss weight applied here, wc = w (1 -+ 1/sqrt 3)/2), with f0, F1 as point
 // pairs and out as node pairs out[ja + 2 ka] = (out[a], out[a + 1]).
@@ -251,8 +251,8 @@ NC_HD void test8_f2(f2 out[4], const f2 f0[4], const f2 F1[4][3], const float wc
 #pragma unroll
   for (int ja = 0; ja < 2; ++ja) {
     const f2 d = fma2(K.c[1], VZB[1][ja], fma2(K.c[0], VZB[0][ja], DZB[ja]));
-    out[ja] = add2(out[ja], sub2(add2(VZB[0][ja], VZB[1][ja]), d));
-    out[ja + 2] = add2(out[ja + 2], d);
+    out[ja] = sub2(add2(VZB[0][ja], VZB[1][ja]), d);
+    out[ja + 2] = d;
   }
 }
 
@@ -267,7 +267,6 @@ NC_HD void test_all_f2(float out[5][8], const f2 f0[4][5], const f2 F1[4][5][3],
       b[P][0] = F1[P][f][0];
       b[P][1] = F1[P][f][1];
       b[P][2] = F1[P][f][2];
-      o[P] = mk2(0.0f, 0.0f);
     }
     test8_f2(o, a, b, wc, K);
 #pragma unroll

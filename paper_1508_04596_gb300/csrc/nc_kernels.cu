@@ -88,12 +88,14 @@ __global__ void __launch_bounds__(ELEM_THREADS) k_elem_res(LevelDev d, ElemConst
   store_elem(d.E, e, out, Y);
 }
 
-// Three blocks per SM (at most 168 registers, a few spilled): 12 warps per SM hide
-// more latency than 8 at 255 registers; measured 9.6 % faster in FP32 and
-// unchanged in FP64.  FP32 takes the packed-pair element routines (two lanes of
-// FP32 arithmetic per instruction).
+// J v: three blocks per SM (at most 168 registers, a few spilled): 12 warps per SM
+// hide more latency than 8 at 255 registers; measured 9.6 % faster in FP32 and
+// unchanged in FP64.  J^T w, whose fluxes keep more values live, takes two blocks
+// per SM and up to 255 registers: 10 % faster in FP32 than three blocks (its
+// spills at 168 registers cost more than the extra warps gain).  FP32 takes the
+// packed-pair element routines (two lanes of FP32 arithmetic per instruction).
 template <typename R, bool TRANSPOSE>
-__global__ void __launch_bounds__(ELEM_THREADS, 3) k_elem_lin(LevelDev d, ElemConst<R> c,
+__global__ void __launch_bounds__(ELEM_THREADS, TRANSPOSE ? 2 : 3) k_elem_lin(LevelDev d, ElemConst<R> c,
                                                            const R* __restrict__ x,
                                                            const R* __restrict__ gam,
                                                            const R* __restrict__ src,

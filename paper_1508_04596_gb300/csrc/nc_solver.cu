@@ -55,8 +55,16 @@ nc_status alloc(nc_ctx* ctx, R** p, long long n) {
 // and beta = sigma_0.  Solve min || beta e1 - H y || by Givens rotations (in
 // place), then store the coefficients of the correction on the raw basis,
 // y_j / sigma_j -> Hd[HD_Y + j].  A vanishing norm or pivot (an exhausted
-// Krylov space) contributes zero.
-__global__ void k_small_ls(double* Hd, int k) {
+// Krylov space) contributes zero.  One warp stages the k columns and the norms
+// in shared memory, then one thread solves there: the elimination is a chain of
+// dependent operations, and in shared memory each costs tens of cycles instead
+// of a round trip to L2.
+constexpr int LS_THREADS = 32;
+__global__ void __launch_bounds__(LS_THREADS) k_small_ls(double* Hd_g, int k) {
+  __shared__ double Hd[HD_SIZE];
+  for (int t = threadIdx.x; t < k * LDH; t += LS_THREADS) Hd[t] = Hd_g[t];
+  for (int t = threadIdx.x; t <= k; t += LS_THREADS) Hd[HD_SIG2 + t] = Hd_g[HD_SIG2 + t];
+  __syncwarp();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double* g = Hd + HD_Y + LDH;  // right-hand side, k + 1 entries
   const double* sig2 = Hd + HD_SIG2;
@@ -102,7 +110,8 @@ __global__ void k_small_ls(double* Hd, int k) {
     const double d = Hd[j + j * LDH];
     Hd[HD_Y + j] = (fabs(d) > 1e-14 * rmax && isfinite(acc)) ? acc / d : 0.0;
   }
-  for (int j = 0; j < k; ++j) Hd[HD_Y + j] *= inv_sig(j);
+  for (int j = 0; j < k; ++j) Hd_g[HD_Y + j] = Hd[HD_Y + j] * inv_sig(j);
+  Hd_g[HD_BETA] = Hd[HD_BETA];
 }
 
 // ------------------------------------------------------------------ level operators
@@ -157,7 +166,7 @@ void smooth(nc_ctx* ctx, int l, bool tr, int k, bool zero_init, cudaStream_t s) 
     varnoldi_update(n, j + 1, (const R*)V, ld, hcol, Hd + HD_SIG2, (const R*)B.diag, w,
                     j + 1 < k ? B.t : (R*)nullptr, Hd + HD_SIG2 + j + 1, ctx->partial, s);
   }
-  k_small_ls<<<1, 1, 0, s>>>(Hd, k);
+  k_small_ls<<<1, LS_THREADS, 0, s>>>(Hd, k);
   // z (+)= D^-1 (V y)
   vcombine(n, k, (const R*)V, ld, Hd + HD_Y, (const R*)B.diag, B.z, !zero_init, s);
 }

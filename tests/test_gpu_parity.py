@@ -444,19 +444,26 @@ def test_mma_update_matches_oracle(nc, n, k, f1):
     assert chg == pytest.approx(np.max(np.abs(host(X) - x)), rel=1e-12)
 
 
-def test_volume_matches_numpy(nc):
-    """Normalised volume constraint (Sec. 3.2) and its gradient against numpy,
-    with and without a design mask; a ragged size."""
+def test_volume_matches_oracle(nc):
+    """Normalised volume constraint (Sec. 3.2) and its gradient through nc_volume
+    against the oracle's (oracle.mma.volume_constraint), with and without a
+    design mask, on a ragged size; a design at exactly the volume fraction gives 0."""
+    from oracle import mma as M
     rng = np.random.default_rng(21)
     n = 33333
     g = rng.uniform(0, 1, n)
     act = rng.uniform(0, 1, n) < 0.3
     gp = nc.Problem(nc.make_params(2, 2, 2, 0.5, 1e3, 0.71), nc.cavity_bcs())
     grad = torch.empty(n, dtype=torch.float64, device="cuda")
-    v = gp.volume(dev(g), torch.tensor(act.astype(np.uint8), device="cuda"), vf=0.05, grad=grad)
-    assert v == pytest.approx(np.sum(1 - g[act]) / (0.05 * act.sum()) - 1, rel=1e-13)
-    assert np.allclose(host(grad), np.where(act, -1 / (0.05 * act.sum()), 0.0), rtol=1e-15, atol=0)
-    assert gp.volume(dev(g), None, vf=0.5) == pytest.approx(np.sum(1 - g) / (0.5 * n) - 1, rel=1e-13)
+    am = torch.tensor(act.astype(np.uint8), device="cuda")
+    v = gp.volume(dev(g), am, vf=0.05, grad=grad)
+    vo, go = M.volume_constraint(g, act, 0.05)
+    assert v == pytest.approx(vo, rel=1e-13)
+    assert np.allclose(host(grad), go, rtol=1e-15, atol=0)
+    assert gp.volume(dev(g), None, vf=0.5) == pytest.approx(M.volume_constraint(g, None, 0.5)[0],
+                                                           rel=1e-13)
+    at_vf = np.where(act, 0.95, g)
+    assert abs(gp.volume(dev(at_vf), am, vf=0.05)) <= 1e-13
 
 
 def test_design_map(nc):

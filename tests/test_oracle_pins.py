@@ -553,6 +553,33 @@ def _mma_instance(rng, n):
     return x, xold1, xold2, low, upp, f1, df0, df1
 
 
+def test_volume_constraint_definition():
+    """Sec. 3.2 volume constraint: satisfied with equality when the solid volume of
+    the design domain is exactly v_f of it, -1 when it is all fluid; elements
+    outside the design domain do not count; the gradient equals central
+    differences (the constraint is linear); the element size cancels."""
+    from oracle import mma as M
+    rng = np.random.default_rng(3)
+    n, vf = 1000, 0.05
+    act = rng.uniform(size=n) < 0.4
+    gam = np.where(act, 1.0 - vf, rng.uniform(size=n))
+    g, dg = M.volume_constraint(gam, act, vf, h=0.1)
+    assert abs(g) <= 1e-12
+    assert M.volume_constraint(np.ones(n), act, vf)[0] == pytest.approx(-1.0, abs=1e-15)
+    gam2 = gam.copy()
+    gam2[~act] = rng.uniform(size=(~act).sum())
+    assert M.volume_constraint(gam2, act, vf)[0] == pytest.approx(g, abs=1e-15)
+    x = rng.uniform(size=n)
+    gx, dgx = M.volume_constraint(x, act, vf, h=0.3)
+    for e in (int(np.nonzero(act)[0][3]), int(np.nonzero(~act)[0][5])):
+        xp, xm = x.copy(), x.copy()
+        xp[e] += 1e-3
+        xm[e] -= 1e-3
+        fd = (M.volume_constraint(xp, act, vf)[0] - M.volume_constraint(xm, act, vf)[0]) / 2e-3
+        assert dgx[e] == pytest.approx(fd, rel=1e-9, abs=1e-13)
+    assert M.volume_constraint(x, act, vf, h=2.0)[0] == pytest.approx(gx, rel=1e-13)
+
+
 def test_mma_subproblem_kkt_and_scipy():
     """MMA (the optimiser of Sec. 3.2): the oracle's step solves its convex
     subproblem.  KKT: each coordinate strictly inside its move limits is
