@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--solve-workload", default=None,
                     help="workload of the state/adjoint design-iteration timing (default: --workload)")
+    ap.add_argument("--ops-once", action="store_true",
+                    help="one J v and one J^T w in --prec at a random BC-consistent state of "
+                         "--workload, nothing else (profiling runs)")
     ap.add_argument("--solve-only", action="store_true",
                     help="only the design-iteration solve block of --workload, printed as JSON")
     ap.add_argument("--jv-only", action="store_true",
@@ -749,6 +752,20 @@ def main():
         prob = nc.Problem(nc.make_params(2, 2, 2, 0.5, 1e3, 0.71), nc.cavity_bcs())
         only = None if args.vectors_only == "both" else args.vectors_only
         print(json.dumps(hbm_kernels(prob, torch.cuda.current_stream(), only=only)))
+        return
+    if args.ops_once:
+        import torch
+        from paper_1508_04596_gb300 import nc, synth
+        cfg = synth.WORKLOADS[args.workload]
+        dt = torch.float64 if args.prec == "f64" else torch.float32
+        prob = nc.Problem.from_workload(args.workload)
+        g = torch.tensor(synth.design(args.workload), dtype=dt, device="cuda")
+        x = torch.tensor(synth.random_state(cfg["nx"], cfg["ny"], cfg["nz"], 1,
+                                            (0.5, 0.5, 0.5, 50, 1)).ravel(), dtype=dt, device="cuda")
+        prob.impose_dirichlet(x)
+        v = torch.randn(prob.ndof, generator=torch.Generator().manual_seed(3)).to("cuda", dt)
+        a, b = prob.jvp(x, g, v), prob.jtvp(x, g, v)
+        print(json.dumps({"jvp_norm": float(a.norm()), "jtvp_norm": float(b.norm())}))
         return
     if args.solve_only:
         import torch

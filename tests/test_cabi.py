@@ -90,3 +90,18 @@ def test_quarter_workloads_have_the_papers_sizes(lib):
         assert cfg["h"] * cfg["nz"] == pytest.approx(1.0)  # unit cavity height
         seen.add(key)
     assert len(seen) == 3
+
+
+def test_fma_probe_rejects_invalid_arguments(lib):
+    """nc_fma_probe checks its arguments before touching the device: an unknown
+    precision, no blocks, an iteration count that is not a positive multiple of
+    16 or a NULL output are NC_ERR_ARG (no GPU needed)."""
+    f = lib.nc_fma_probe
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]
+    dummy = ctypes.c_void_p(16)  # never dereferenced: every call below is rejected first
+    assert f(7, 1, 16, dummy, None) == 1
+    assert f(0, 0, 16, dummy, None) == 1
+    assert f(1, 1, 15, dummy, None) == 1
+    assert f(1, 1, 0, dummy, None) == 1
+    assert f(0, 1, 16, None, None) == 1
