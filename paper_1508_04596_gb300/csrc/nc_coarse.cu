@@ -34,10 +34,8 @@ __global__ void k_coarse_elem_jac(LevelDev d, ElemConst<double> c, const R* __re
   const long long e = blockIdx.x;
   const int k = threadIdx.x;
   if (k >= 40 || e >= d.E) return;
-  const int i = (int)(e % d.nx);
-  const long long t = e / d.nx;
-  const int j = (int)(t % d.ny);
-  const int kk = (int)(t / d.ny);
+  int i, j, kk;
+  elem_ijk(d, e, i, j, kk);
   const long long sy = d.nx + 1, sz = (long long)(d.nx + 1) * (d.ny + 1);
   const long long n0 = i + sy * (j + (long long)(d.ny + 1) * kk);
   double xe[5][8], ve[5][8], out[5][8];
@@ -166,10 +164,8 @@ nc_status coarse_setup(nc_ctx* ctx, Level& L, const R* x, const R* gam, const R*
   std::vector<double> A((size_t)n * n, 0.0);
   const long long sy = d.nx + 1, sz = (long long)(d.nx + 1) * (d.ny + 1);
   for (long long e = 0; e < E; ++e) {
-    const int i = (int)(e % d.nx);
-    const long long t = e / d.nx;
-    const int j = (int)(t % d.ny);
-    const int kk = (int)(t / d.ny);
+    int i, j, kk;
+    elem_ijk(d, e, i, j, kk);
     const long long n0 = i + sy * (j + (long long)(d.ny + 1) * kk);
     long long nodes[8];
     for (int a = 0; a < 8; ++a) nodes[a] = n0 + (a & 1) + ((a >> 1) & 1) * sy + ((a >> 2) & 1) * sz;
@@ -218,10 +214,8 @@ nc_status coarse_setup_stencil(nc_ctx* ctx, Level& L, const R* S, R** inv_dev, c
   // of the stencil already
   std::vector<double> A((size_t)n * n, 0.0);
   for (long long node = 0; node < Nn; ++node) {
-    const int i = (int)(node % (d.nx + 1));
-    const long long t = node / (d.nx + 1);
-    const int j = (int)(t % (d.ny + 1));
-    const int k = (int)(t / (d.ny + 1));
+    int i, j, k;
+    node_ijk(d, node, i, j, k);
     for (int o = 0; o < 27; ++o) {
       const int ii = i + o % 3 - 1, jj = j + (o / 3) % 3 - 1, kk = k + o / 9 - 1;
       if (ii < 0 || ii > d.nx || jj < 0 || jj > d.ny || kk < 0 || kk > d.nz) continue;

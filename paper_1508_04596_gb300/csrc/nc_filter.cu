@@ -47,10 +47,8 @@ __global__ void k_helm_apply(LevelDev d, HelmCoef c, const double* __restrict__ 
                              double* __restrict__ y, double* __restrict__ diag) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= d.Nn) return;
-  const int i = (int)(n % (d.nx + 1));
-  const long long t = n / (d.nx + 1);
-  const int j = (int)(t % (d.ny + 1));
-  const int k = (int)(t / (d.ny + 1));
+  int i, j, k;
+  node_ijk(d, n, i, j, k);
   const long long sy = d.nx + 1, sz = (long long)(d.nx + 1) * (d.ny + 1);
   double acc = 0.0, dg = 0.0;
   for (int a = 0; a < 8; ++a) {  // the node is local corner a of element (i-ia, j-ja, k-ka)
@@ -72,10 +70,8 @@ __global__ void k_helm_apply(LevelDev d, HelmCoef c, const double* __restrict__ 
 __global__ void k_helm_rhs(LevelDev d, const double* __restrict__ rho, double* __restrict__ b) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= d.Nn) return;
-  const int i = (int)(n % (d.nx + 1));
-  const long long t = n / (d.nx + 1);
-  const int j = (int)(t % (d.ny + 1));
-  const int k = (int)(t / (d.ny + 1));
+  int i, j, k;
+  node_ijk(d, n, i, j, k);
   double acc = 0.0;
   for (int a = 0; a < 8; ++a) {
     const int ie = i - (a & 1), je = j - ((a >> 1) & 1), ke = k - ((a >> 2) & 1);
@@ -89,10 +85,8 @@ __global__ void k_helm_rhs(LevelDev d, const double* __restrict__ rho, double* _
 __global__ void k_elem_mean(LevelDev d, const double* __restrict__ x, double* __restrict__ g) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= d.E) return;
-  const int i = (int)(e % d.nx);
-  const long long t = e / d.nx;
-  const int j = (int)(t % d.ny);
-  const int k = (int)(t / d.ny);
+  int i, j, k;
+  elem_ijk(d, e, i, j, k);
   const long long sy = d.nx + 1, sz = (long long)(d.nx + 1) * (d.ny + 1);
   const long long n0 = i + sy * (j + (long long)(d.ny + 1) * k);
   double acc = 0.0;

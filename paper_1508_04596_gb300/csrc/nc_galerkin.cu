@@ -29,13 +29,6 @@ constexpr int GT = 256;
 // SM); blocks of 128 halve the imbalance between SMs.
 constexpr int AT = 128;
 
-__device__ __forceinline__ void node_ijk(const LevelDev& d, long long n, int& i, int& j, int& k) {
-  i = (int)(n % (d.nx + 1));
-  const long long t = n / (d.nx + 1);
-  j = (int)(t % (d.ny + 1));
-  k = (int)(t / (d.ny + 1));
-}
-
 __device__ __forceinline__ long long nid(const LevelDev& d, int i, int j, int k) {
   return i + (long long)(d.nx + 1) * (j + (long long)(d.ny + 1) * k);
 }

@@ -37,6 +37,35 @@ struct LevelDev {
   double q;             // patch flux (NC_PATCH_FLUX)
 };
 
+#if defined(__CUDACC__)
+// (i, j, k) of a linear index idx = i + n0 (j + n1 k) below total.  With total
+// below 2^32 (every grid that fits a GPU's memory in practice) this takes 32-bit
+// unsigned division, which costs a fraction of the 64-bit routine on the GPU;
+// the test is the same for every thread of a launch, so it does not diverge.
+__host__ __device__ __forceinline__ void split3(long long idx, long long total, int n0, int n1, int& i,
+                                       int& j, int& k) {
+  if (total <= 0xffffffffLL) {
+    const unsigned u = (unsigned)idx, t = u / (unsigned)n0, kk = t / (unsigned)n1;
+    i = (int)(u - t * (unsigned)n0);
+    j = (int)(t - kk * (unsigned)n1);
+    k = (int)kk;
+  } else {
+    const long long t = idx / n0;
+    i = (int)(idx - t * n0);
+    j = (int)(t % n1);
+    k = (int)(t / n1);
+  }
+}
+// element e = i + nx (j + ny k)
+__host__ __device__ __forceinline__ void elem_ijk(const LevelDev& d, long long e, int& i, int& j, int& k) {
+  split3(e, d.E, d.nx, d.ny, i, j, k);
+}
+// node n = i + (nx+1) (j + (ny+1) k)
+__host__ __device__ __forceinline__ void node_ijk(const LevelDev& d, long long n, int& i, int& j, int& k) {
+  split3(n, d.Nn, d.nx + 1, d.ny + 1, i, j, k);
+}
+#endif
+
 template <typename R>
 struct Vec {
   R* p = nullptr;

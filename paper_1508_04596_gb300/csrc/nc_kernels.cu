@@ -26,10 +26,8 @@ __device__ __forceinline__ long long node_id(const LevelDev& d, int i, int j, in
 template <typename R>
 __device__ __forceinline__ void load_elem(const LevelDev& d, const R* __restrict__ x, long long e,
                                           R xe[5][8], bool mask) {
-  const int i = (int)(e % d.nx);
-  const long long t = e / d.nx;
-  const int j = (int)(t % d.ny);
-  const int k = (int)(t / d.ny);
+  int i, j, k;
+  elem_ijk(d, e, i, j, k);
   const long long n0 = node_id(d, i, j, k);
   const long long sy = d.nx + 1, sz = (long long)(d.nx + 1) * (d.ny + 1);
 #pragma unroll
@@ -46,10 +44,8 @@ __device__ __forceinline__ void load_elem(const LevelDev& d, const R* __restrict
 
 // node of local index a (bit 0: +x, bit 1: +y, bit 2: +z) of element e
 __device__ __forceinline__ long long elem_node(const LevelDev& d, long long e, int a) {
-  const int i = (int)(e % d.nx);
-  const long long t = e / d.nx;
-  const int j = (int)(t % d.ny);
-  const int k = (int)(t / d.ny);
+  int i, j, k;
+  elem_ijk(d, e, i, j, k);
   return node_id(d, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
 }
 
@@ -215,10 +211,8 @@ __global__ void __launch_bounds__(NODE_THREADS) k_assemble_column(LevelDev d, in
                                                                   R* __restrict__ S) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= d.Nn) return;
-  const int i = (int)(n % (d.nx + 1));
-  const long long t = n / (d.nx + 1);
-  const int j = (int)(t % (d.ny + 1));
-  const int k = (int)(t / (d.ny + 1));
+  int i, j, k;
+  node_ijk(d, n, i, j, k);
   const int b = col / 5, g = col % 5;
   const uint8_t fl = d.flag[n];
 #pragma unroll
@@ -281,10 +275,8 @@ __global__ void __launch_bounds__(NODE_THREADS) k_gather(LevelDev d, const R* __
                                                          const R* __restrict__ xv, R* out) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= d.Nn) return;
-  const int i = (int)(n % (d.nx + 1));
-  const long long t = n / (d.nx + 1);
-  const int j = (int)(t % (d.ny + 1));
-  const int k = (int)(t / (d.ny + 1));
+  int i, j, k;
+  node_ijk(d, n, i, j, k);
   R acc[5] = {R(0), R(0), R(0), R(0), R(0)};
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
@@ -347,10 +339,8 @@ __global__ void k_objective_grad(LevelDev d, double* g, double inv_area) {
 __global__ void k_source_grad(LevelDev d, const double* __restrict__ src, double* g) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= d.Nn) return;
-  const int i = (int)(n % (d.nx + 1));
-  const long long t = n / (d.nx + 1);
-  const int j = (int)(t % (d.ny + 1));
-  const int k = (int)(t / (d.ny + 1));
+  int i, j, k;
+  node_ijk(d, n, i, j, k);
   double acc = 0.0;
   for (int a = 0; a < 8; ++a) {
     const int ie = i - (a & 1), je = j - ((a >> 1) & 1), ke = k - ((a >> 2) & 1);
@@ -367,10 +357,8 @@ template <typename R>
 __global__ void k_restrict(LevelDev f, const R* __restrict__ rf, LevelDev c, R* rc) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= c.Nn) return;
-  const int I = (int)(n % (c.nx + 1));
-  const long long t = n / (c.nx + 1);
-  const int J = (int)(t % (c.ny + 1));
-  const int K = (int)(t / (c.ny + 1));
+  int I, J, K;
+  node_ijk(c, n, I, J, K);
   const uint8_t cfl = c.flag[n];
   R acc[5] = {R(0), R(0), R(0), R(0), R(0)};
   for (int dk = -1; dk <= 1; ++dk) {
@@ -401,10 +389,8 @@ template <typename R>
 __global__ void k_prolong_add(LevelDev c, const R* __restrict__ zc, LevelDev f, R* zf) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= f.Nn) return;
-  const int i = (int)(n % (f.nx + 1));
-  const long long t = n / (f.nx + 1);
-  const int j = (int)(t % (f.ny + 1));
-  const int k = (int)(t / (f.ny + 1));
+  int i, j, k;
+  node_ijk(f, n, i, j, k);
   const uint8_t ffl = f.flag[n];
   const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1, k0 = k >> 1,
             k1 = (k + 1) >> 1;
@@ -433,10 +419,8 @@ template <typename R>
 __global__ void k_inject(LevelDev f, const R* __restrict__ xf, LevelDev c, R* xc) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= c.Nn) return;
-  const int I = (int)(n % (c.nx + 1));
-  const long long t = n / (c.nx + 1);
-  const int J = (int)(t % (c.ny + 1));
-  const int K = (int)(t / (c.ny + 1));
+  int I, J, K;
+  node_ijk(c, n, I, J, K);
   const long long m = node_id(f, 2 * I, 2 * J, 2 * K);
 #pragma unroll
   for (int q = 0; q < 5; ++q) xc[q * c.Nn + n] = xf[q * f.Nn + m];
@@ -446,10 +430,8 @@ template <typename R>
 __global__ void k_coarsen_elem(LevelDev f, const R* __restrict__ gf, LevelDev c, R* gc) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= c.E) return;
-  const int I = (int)(e % c.nx);
-  const long long t = e / c.nx;
-  const int J = (int)(t % c.ny);
-  const int K = (int)(t / c.ny);
+  int I, J, K;
+  elem_ijk(c, e, I, J, K);
   R acc = R(0);
   for (int a = 0; a < 8; ++a) {
     const int i = 2 * I + (a & 1), j = 2 * J + ((a >> 1) & 1), k = 2 * K + ((a >> 2) & 1);

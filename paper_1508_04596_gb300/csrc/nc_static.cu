@@ -64,10 +64,8 @@ struct FlagSpec {
 __global__ void k_static_flags(LevelDev d, FlagSpec fs, uint8_t* flag) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= d.Nn) return;
-  const int i = (int)(n % (d.nx + 1));
-  const long long t = n / (d.nx + 1);
-  const int j = (int)(t % (d.ny + 1));
-  const int k = (int)(t / (d.ny + 1));
+  int i, j, k;
+  node_ijk(d, n, i, j, k);
   const bool on[6] = {i == 0, i == d.nx, j == 0, j == d.ny, k == 0, k == d.nz};
   unsigned m = 0;
   for (int f = 0; f < 6; ++f) {

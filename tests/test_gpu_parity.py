@@ -92,6 +92,30 @@ def test_bc_flags_symmetry_and_pin(nc):
         assert np.array_equal(((fl >> f) & 1).astype(bool), prob.dmask[f])
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_operators_interior_pin(nc, prec):
+    """Pressure pinned at an interior node (the one Dirichlet node that can lie off
+    the boundary): J v and J^T w against the oracle's Jacobian, and the residual."""
+    nx, ny, nz = 36, 10, 9
+    pin = 5 + (nx + 1) * (4 + (ny + 1) * 3)
+    bc = G.BCs(patch_mode=G.PATCH_FLUX, p_pin=pin)
+    prob, _ = oracle_problem(nx, ny, nz, 1.0 / nx, 1e4, 0.71, bc=bc)
+    b = nc.cavity_bcs(nc.PATCH_FLUX, 1.0)
+    b.p_pin = pin
+    gp = nc.Problem(nc.make_params(nx, ny, nz, 1.0 / nx, 1e4, 0.71, **synth.MATERIAL), b)
+    assert ((gp.bc_flags()[pin] >> 3) & 1) == 1
+    gam = synth.smoothed_random(nx, ny, nz, 1.0 / nx, 31)
+    x = random_bc_state(prob, 32)
+    J = prob.jacobian(x, gam)
+    dt, tol = (torch.float64, TOL64) if prec == "f64" else (torch.float32, TOL32)
+    xd, gd = dev(x, dt), dev(gam, dt)
+    v = np.random.default_rng(33).standard_normal(prob.g.ndof)
+    vd = dev(v, dt)
+    assert rel(host(gp.residual(xd, gd), (5, -1)), prob.residual(x, gam)) <= tol
+    assert rel(host(gp.jvp(xd, gd, vd)), J @ v) <= tol
+    assert rel(host(gp.jtvp(xd, gd, vd)), J.T @ v) <= tol
+
+
 @pytest.mark.parametrize("c", CASES)
 def test_residual_fp64(nc, c):
     prob, bc, gp, gam, x = make_pair(nc, c)
@@ -142,7 +166,16 @@ WIDE_CASES = [
 ]
 
 
-@pytest.mark.parametrize("c", CASES + WIDE_CASES)
+# wider grids: an x-row of exactly one warp, x-rows that end inside a warp (a
+# warp spanning two rows), ragged in y and z
+WARP_ROW_CASES = [
+    dict(nx=32, ny=8, nz=4, Gr=1e4, patch="dirichlet", seed=21),
+    dict(nx=40, ny=9, nz=35, Gr=1e5, patch="flux", seed=22),
+    dict(nx=67, ny=13, nz=6, Gr=1e3, patch="dirichlet", seed=23),
+]
+
+
+@pytest.mark.parametrize("c", CASES + WIDE_CASES + WARP_ROW_CASES)
 def test_fp32_operators(nc, c):
     prob, bc, gp, gam, x = make_pair(nc, c)
     J = prob.jacobian(x, gam)
@@ -150,9 +183,45 @@ def test_fp32_operators(nc, c):
     xd, gd = dev(x, f), dev(gam, f)
     v = np.random.default_rng(3).standard_normal(prob.g.ndof)
     assert rel(host(gp.residual(xd, gd), (5, -1)), prob.residual(x, gam)) <= TOL32
-    assert rel(host(gp.jvp(xd, gd, dev(v, f))), J @ v) <= TOL32
-    assert rel(host(gp.jtvp(xd, gd, dev(v, f))), J.T @ v) <= TOL32
+    vd = dev(v, f)
+    jv, jtv = gp.jvp(xd, gd, vd), gp.jtvp(xd, gd, vd)
+    assert rel(host(jv), J @ v) <= TOL32
+    assert rel(host(jtv), J.T @ v) <= TOL32
+    # deterministic: fixed summation order, no atomics
+    assert torch.equal(gp.jvp(xd, gd, vd), jv) and torch.equal(gp.jtvp(xd, gd, vd), jtv)
     assert rel(host(gp.diag(xd, gd)), J.diagonal()) <= TOL32
+
+
+def test_fp32_products_sampled_lines(nc):
+    """FP32 J v and J^T w at 100 x 40 x 30 (warps straddle x-rows, 120,000
+    elements): whole x-rows (every lane position meets a warp boundary somewhere)
+    and z-lines against element-by-element oracle rows, plus random nodes; and
+    bitwise repeatable."""
+    nx, ny, nz = 100, 40, 30
+    prob, bc = oracle_problem(nx, ny, nz, 1.0 / nz, 1e5, 0.71, patch_mode="flux")
+    g = prob.g
+    rng = np.random.default_rng(41)
+    gam = rng.uniform(0.0, 1.0, g.E)
+    x = random_bc_state(prob, 42)
+    v = rng.standard_normal((5, g.Nn))
+    vm = np.where(prob.dmask, 0.0, v)
+    lines = [g.node(i, j, k) for (i, j) in [(32, 16), (64, 4), (10, 10), (0, 0), (100, 40),
+                                            (99, 7)] for k in range(nz + 1)]
+    rows = [g.node(i, j, k) for (j, k) in [(4, 15), (17, 29), (0, 30), (40, 0), (23, 1)]
+            for i in range(nx + 1)]
+    nodes = np.unique(np.array(lines + rows + list(rng.choice(g.Nn, size=40, replace=False))))
+    gp = nc.Problem(nc.make_params(nx, ny, nz, 1.0 / nz, 1e5, 0.71, **synth.MATERIAL),
+                    nc.cavity_bcs(nc.PATCH_FLUX, 1.0))
+    f = torch.float32
+    X, Gm, V = dev(x, f), dev(gam, f), dev(v, f)
+    idx = torch.tensor(nodes, device="cuda")
+    for kind, op in (("jvp", gp.jvp), ("jtvp", gp.jtvp)):
+        got = op(X, Gm, V)
+        assert torch.equal(op(X, Gm, V), got)
+        ref = np.where(prob.dmask[:, nodes], v[:, nodes], sampled_rows(g, prob.prm, x, gam, vm,
+                                                                        nodes, kind))
+        err = rel(host(got.view(5, -1)[:, idx]), ref)
+        assert err <= TOL32, (kind, err)
 
 
 @pytest.mark.parametrize("c", CASES)
