@@ -34,11 +34,12 @@ import numpy as np  # noqa: E402
 
 NAPPLY = 16  # J v applications per step
 DEFAULT_WORKLOAD = "tall192x192x384_gr1e6"
-# Operation counts per element (one +, -, * or / = 1 flop; an FMA = 2), of the
-# element routines in csrc/nc_element.cuh, counted by instantiating them with a
-# counting number type.
-FLOPS_PER_ELEM = {"residual": 1893, "jvp": 3235, "jtvp": 3356, "diag": 7272, "sens": 3057,
-                  "linearize": 875, "jvp_lin": 2377}
+# Operation counts per element (one +, -, *, / or reciprocal square root = 1
+# flop; an FMA = 2), of the element routines in csrc/nc_element.cuh, counted by
+# instantiating them with a counting number type (tests/host/element_flop_count.cpp;
+# tests/test_element_host.py checks that these figures match it).
+FLOPS_PER_ELEM = {"residual": 1794, "jvp": 3076, "jtvp": 3196, "diag": 6981, "sens": 2892,
+                  "linearize": 816, "jvp_lin": 2264, "jtvp_lin": 2384}
 # ALU peaks (whole GPU) from unit counts and the maximum SM clock: 152 SMs x 128
 # FP32 lanes x 2 flop x 2.07 GHz, and 152 SMs x 2 FP64 FMA units x 2 flop x 2.07 GHz
 # (1.259 TFLOP/s, the GB300's nominal FP64 rate of 1.25).  nc_fma_probe measures
@@ -518,7 +519,7 @@ def run_ours(args, rank, world):
         prob.linearize(x64, gam64)  # leave no stale reference to the step's inputs
     free, _ = torch.cuda.mem_get_info()
     S_bytes = 675 * 8 * prob.Nn
-    if free > S_bytes + 2 * 8 * 154 * prob.E + (4 << 30):
+    if free > S_bytes + 2 * 8 * 156 * prob.E + (4 << 30):
         extra["assembled"] = assembled_operator(
             prob, x64, gam64, V.double(), ops["jvp"]["ms"],
             t_step / NAPPLY if args.prec == "f64" else None, stream,

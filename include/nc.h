@@ -214,9 +214,10 @@ nc_status nc_sensitivity(nc_ctx* ctx, const double* x, const double* gamma,
  * parameters, boundary conditions, inputs and output (device pointers, same
  * layouts and prec as nc_jvp), and the scratch is a fixed device array of
  * NC_STATIC_SCRATCH_BYTES inside the library, held by every GPU that loads it
- * until the process exits.  The problem must fit: round_up(Nn, 256) + 40 * E *
- * sizeof(element) <= NC_STATIC_SCRATCH_BYTES (about 200,000 elements in FP64,
- * 400,000 in FP32), else NC_ERR_SIZE and nothing is launched.  The first call on
+ * until the process exits.  The problem must fit: round_up(Nn, 256) +
+ * 40 * round_up(E, 32) * sizeof(element) <= NC_STATIC_SCRATCH_BYTES (about
+ * 200,000 elements in FP64, 400,000 in FP32), else NC_ERR_SIZE and nothing is
+ * launched.  The first call on
  * a device looks the array's device address up (once per device, with that
  * device current); make that first call before any stream capture.  The array
  * keeps the last call's contents; nothing in it needs to start at zero.  All

@@ -256,7 +256,7 @@ nc_status nc_setup(const nc_params* prm, const nc_bcs* bcs, nc_ctx** out) {
     ++lvl;
   }
   const Level& L0 = ctx->lv[0];
-  if ((st = dev_alloc(ctx, &ctx->Y, 40 * L0.d.E)) != NC_OK) { nc_destroy(ctx); return st; }
+  if ((st = dev_alloc(ctx, &ctx->Y, scratch_len(L0.d.E))) != NC_OK) { nc_destroy(ctx); return st; }
   if ((st = dev_alloc(ctx, &ctx->partial, (long long)(MAX_RESTART + 2) * RED_BLOCKS_MAX)) != NC_OK ||
       (st = dev_alloc(ctx, &ctx->dscal, (long long)(MAX_RESTART + 2) * 4)) != NC_OK) {
     nc_destroy(ctx);

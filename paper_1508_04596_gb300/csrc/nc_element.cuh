@@ -22,6 +22,16 @@
 // the dtau/du_e term of App. B), its adjoint (J^T w), the diagonal of J_e and
 // the design derivative lambda^T dr_e/dgamma_e (with dtau/dgamma_e).  It is
 // plain arithmetic on register arrays, usable from host and device code.
+//
+// Scaling.  Point gradients are kept in reference units, h grad (the nodal
+// differences of the tensor-product stages, with no division by h), and so are
+// the quantities formed from them: the strong residuals rM, rT and the value-slot
+// fluxes f0 are h times their physical values.  The coefficients that meet them
+// carry the compensating powers of h: alpha_e and the source s enter as h alpha,
+// h s; tau, tau_T and K as tau/h, tau_T/h, K/h; the buoyancy vector as h beta e^g;
+// the viscous weights as Pr wh/h; the value-slot Gauss weights as w/h.  The
+// element rows come out in physical units.  This removes the 12 multiplications
+// by 1/h per field and element that physical gradients would cost.
 #pragma once
 #include <cmath>
 
@@ -38,15 +48,16 @@ struct ElemConst {
   R inv_h;      // 1/h
   R wq;         // Gauss weight (h/2)^3
   R wh;         // wq / h: weight of the gradient-slot fluxes F1
-  R wc[2];      // wq * (1 -+ 1/sqrt 3)/2: the Gauss weight times the 1-D shape-function
-                // weights of the value-slot fluxes f0 (applied on the test side)
+  R wc[2];      // (wq/h) (1 -+ 1/sqrt 3)/2: the Gauss weight times the 1-D shape-function
+                // weights of the (h-scaled) value-slot fluxes f0 (applied on the test side)
   R Pr, beta;   // Pr, Gr Pr^2
   R eg[3];      // unit gravity direction
-  R beg[3];     // beta * eg
-  R prw, prw2;  // Pr wh, 2 Pr wh
-  R inv16h2;    // 1/(4h)^2      : tau1^-2 = S * inv16h2
-  R t2inv2;     // (4 Pr/h^2)^2  : tau2^-2
-  R k2c;        // (4/h^2)^2     : (h^2/(4K))^-2 = K^2 * k2c
+  R beg[3];     // h beta eg (buoyancy in the h-scaled strong residual)
+  R prw, prw2;  // Pr wh/h, 2 Pr wh/h (viscous fluxes of reference gradients)
+  R h;          // element edge
+  R prh;        // Pr/h: the viscous cotangent weight on reference gradients
+  R wdt;        // wh/16: weight of the tau derivative terms in scaled units
+  R t2s;        // (4 Pr/h)^2 = h^2 tau2^-2: (tau/h)^-2 = S/16 + t2s + (h alpha)^2
   R amax, qa, qf, Ck;
 };
 
@@ -83,7 +94,8 @@ NC_HD constexpr double gsgn(int i) { return i ? 1.0 : -1.0; }
 // x0 + c (x1 - x0) with c = GW[q] (the shape-function weight of the "+" node), and
 // the same difference (x1 - x0) is the derivative along that axis, so values and
 // gradients share their differences (a tensor-product factorisation of the
-// 2x2x2 rule).  Gradients carry 1/h.  interp_pair takes one pair of points
+// 2x2x2 rule).  Gradients are reference differences (h grad, see Scaling
+// above).  interp_pair takes one pair of points
 // (qy, qz fixed, qx = 0, 1); the diagonal of J uses it, every other element
 // routine takes all 8 points at once (interp8 below).
 constexpr double GW0 = 0.21132486540518711775;  // (1 - 1/sqrt 3)/2: weight of node 1 at point 0
@@ -91,7 +103,7 @@ constexpr double GW1 = 0.78867513459481288225;  // (1 + 1/sqrt 3)/2: weight of n
 NC_HD constexpr double gw(int q) { return q ? GW1 : GW0; }
 
 template <typename R>
-NC_HD void interp_pair(const R x[8], R inv_h, R cy, R cz, R val[2], R& gx, R gy[2], R gz[2]) {
+NC_HD void interp_pair(const R x[8], R cy, R cz, R val[2], R& gx, R gy[2], R gz[2]) {
   const R c0 = R(GW0), c1 = R(GW1);
   // z differences and interpolation at qz; index [ia][ja] <-> a = ia + 2 ja (+4 ka)
   const R dz00 = x[4] - x[0], dz10 = x[5] - x[1], dz01 = x[6] - x[2], dz11 = x[7] - x[3];
@@ -104,14 +116,14 @@ NC_HD void interp_pair(const R x[8], R inv_h, R cy, R cz, R val[2], R& gx, R gy[
   const R dx = y1 - y0;
   val[0] = y0 + c0 * dx;
   val[1] = y0 + c1 * dx;
-  gx = dx * inv_h;
+  gx = dx;
   const R ddy = dy1 - dy0;
-  gy[0] = (dy0 + c0 * ddy) * inv_h;
-  gy[1] = (dy0 + c1 * ddy) * inv_h;
+  gy[0] = dy0 + c0 * ddy;
+  gy[1] = dy0 + c1 * ddy;
   const R zy0 = dz00 + cy * (dz01 - dz00), zy1 = dz10 + cy * (dz11 - dz10);
   const R ddz = zy1 - zy0;
-  gz[0] = (zy0 + c0 * ddz) * inv_h;
-  gz[1] = (zy0 + c1 * ddz) * inv_h;
+  gz[0] = zy0 + c0 * ddz;
+  gz[1] = zy0 + c1 * ddz;
 }
 
 // Quadrature-point state: u, G[i][j] = d_j u_i, p, grad p, T, grad T.
@@ -121,9 +133,9 @@ struct QP {
 };
 
 template <typename R>
-NC_HD void interp_field_pair(const R x[8], R inv_h, R cy, R cz, R v[2], R g[2][3]) {
+NC_HD void interp_field_pair(const R x[8], R cy, R cz, R v[2], R g[2][3]) {
   R val[2], gx, gy[2], gz[2];
-  interp_pair<R>(x, inv_h, cy, cz, val, gx, gy, gz);
+  interp_pair<R>(x, cy, cz, val, gx, gy, gz);
   v[0] = val[0];
   v[1] = val[1];
   g[0][0] = gx;
@@ -135,11 +147,11 @@ NC_HD void interp_field_pair(const R x[8], R inv_h, R cy, R cz, R v[2], R g[2][3
 }
 
 template <typename R>
-NC_HD void interp_all_pair(const R xe[5][8], R inv_h, R cy, R cz, QP<R> q[2]) {
+NC_HD void interp_all_pair(const R xe[5][8], R cy, R cz, QP<R> q[2]) {
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     R v[2], g[2][3];
-    interp_field_pair<R>(xe[i], inv_h, cy, cz, v, g);
+    interp_field_pair<R>(xe[i], cy, cz, v, g);
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       q[s].u[i] = v[s];
@@ -150,7 +162,7 @@ NC_HD void interp_all_pair(const R xe[5][8], R inv_h, R cy, R cz, QP<R> q[2]) {
   }
   {
     R v[2], g[2][3];
-    interp_field_pair<R>(xe[3], inv_h, cy, cz, v, g);
+    interp_field_pair<R>(xe[3], cy, cz, v, g);
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       q[s].p = v[s];
@@ -161,7 +173,7 @@ NC_HD void interp_all_pair(const R xe[5][8], R inv_h, R cy, R cz, QP<R> q[2]) {
   }
   {
     R v[2], g[2][3];
-    interp_field_pair<R>(xe[4], inv_h, cy, cz, v, g);
+    interp_field_pair<R>(xe[4], cy, cz, v, g);
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       q[s].T = v[s];
@@ -172,8 +184,10 @@ NC_HD void interp_all_pair(const R xe[5][8], R inv_h, R cy, R cz, QP<R> q[2]) {
   }
 }
 
-// Element coefficients shared by all Gauss points; wtau, wtauT, wK are tau,
-// tau_T and K times the F1 weight wh.
+// Element coefficients shared by all Gauss points, in the scaled units of the
+// point quantities (see Scaling): alpha = h alpha_e, tau = tau_e/h,
+// tau_T = tau_T,e/h, K = K_e/h, s = h s_e; wtau, wtauT, wK are tau, tau_T and K
+// times the F1 weight wh.
 template <typename R>
 struct ElemCoef {
   R alpha, K, tau, tauT, s;
@@ -196,11 +210,13 @@ NC_HD ElemCoef<R> elem_coef(const R xe[5][8], R gam, R s, const ElemConst<R>& c,
 #pragma unroll
     for (int a = 0; a < 8; ++a) acc += xe[i][a] * xe[i][a];
   S = acc;
-  k.alpha = alpha_of(gam, c);
-  k.K = K_of(gam, c);
-  k.tau = nc_rsqrt(S * c.inv16h2 + c.t2inv2 + k.alpha * k.alpha);
-  k.tauT = nc_rsqrt(S * c.inv16h2 + k.K * k.K * c.k2c);
-  k.s = s;
+  k.alpha = c.h * alpha_of(gam, c);
+  k.K = c.inv_h * K_of(gam, c);
+  // (tau_e/h)^-2 = h^2 (S/(4h)^2 + (4 Pr/h^2)^2 + alpha_e^2) and
+  // (tau_T,e/h)^-2 = h^2 (S/(4h)^2 + (4 K_e/h^2)^2) in the scaled coefficients
+  k.tau = nc_rsqrt(S * R(0.0625) + c.t2s + k.alpha * k.alpha);
+  k.tauT = nc_rsqrt(S * R(0.0625) + k.K * k.K * R(16));
+  k.s = c.h * s;
   scale_coef(k, c);
   return k;
 }
@@ -353,9 +369,9 @@ NC_HD void flux_adjoint_rm(const QP<R>& q, const R rM[3], R rT, const QP<R>& t,
     gTb[j] = k.K * C1[4][j] + rTb * q.u[j];
   }
   {
-    const R g01 = c.Pr * (C1[0][1] + C1[1][0]), g02 = c.Pr * (C1[0][2] + C1[2][0]);
-    const R g12 = c.Pr * (C1[1][2] + C1[2][1]);
-    const R p2 = R(2) * c.Pr;
+    const R g01 = c.prh * (C1[0][1] + C1[1][0]), g02 = c.prh * (C1[0][2] + C1[2][0]);
+    const R g12 = c.prh * (C1[1][2] + C1[2][1]);
+    const R p2 = R(2) * c.prh;
     Gb[0][0] = p2 * C1[0][0] + c0[3];
     Gb[1][1] = p2 * C1[1][1] + c0[3];
     Gb[2][2] = p2 * C1[2][2] + c0[3];
@@ -410,16 +426,15 @@ NC_HD R point_sens(const QP<R>& q, const QP<R>& t, const ElemCoef<R>& k, R dalph
   }
   R f0[5], F1[5][3];
   flux_tangent<R, true>(q, zero, k, dalpha, dK, dtau, dtauT, c, f0, F1);
-  // f0 carries no weight: multiply by w once; F1 carries w/h and the test
-  // gradient t carries 1/h: multiply by h once
-  const R h = R(1) / c.inv_h;
+  // f0 (h-scaled) carries no weight: multiply by w/h once; F1 carries w/h and
+  // meets the test gradient t in reference units, which supplies the missing h
   R acc = f0[0] * t.u[0] + f0[1] * t.u[1] + f0[2] * t.u[2] + f0[3] * t.p + f0[4] * t.T;
   R acc1 = R(0);
 #pragma unroll
   for (int j = 0; j < 3; ++j)
     acc1 += F1[0][j] * t.G[0][j] + F1[1][j] * t.G[1][j] + F1[2][j] * t.G[2][j] +
             F1[3][j] * t.gp[j] + F1[4][j] * t.gT[j];
-  return c.wq * acc + acc1 * h;
+  return c.wh * acc + acc1;
 }
 
 // ---------------------------------------------------------------------------- linearisation cache
@@ -428,10 +443,12 @@ NC_HD R point_sens(const QP<R>& q, const QP<R>& t, const ElemCoef<R>& k, R dalph
 // and the element's tau, tau_T can be computed once per linearisation and read
 // back by each product instead of being re-interpolated.  Layout: point g' =
 // 2 * pair + qx (pairs in the order (qy, qz) = (0,0), (1,0), (0,1), (1,1)),
-// LIN_GP values per point (u[3], G[3][3], gT[3], rM[3], rT), then tau, tau_T;
+// LIN_GP values per point (u[3], G[3][3], gT[3], rM[3], rT), then tau, tau_T,
+// alpha, K (all in the scaled units of the point quantities, see Scaling; alpha
+// and K are stored so that the products need no division);
 // slot s of an element is stored at cache[s * stride].
 constexpr int LIN_GP = 19;
-constexpr int LIN_SLOTS = 8 * LIN_GP + 2;
+constexpr int LIN_SLOTS = 8 * LIN_GP + 4;
 
 template <typename R>
 NC_HD void load_lin_pair(const R* cache, long long stride, int P, QP<R> q[2], R rM[2][3], R rT[2]) {
@@ -458,11 +475,11 @@ NC_HD void load_lin_pair(const R* cache, long long stride, int P, QP<R> q[2], R 
 template <typename R>
 NC_HD ElemCoef<R> lin_coef(const R* cache, long long stride, R gam, R s, const ElemConst<R>& c) {
   ElemCoef<R> k;
-  k.alpha = alpha_of(gam, c);
-  k.K = K_of(gam, c);
   k.tau = cache[(long long)(8 * LIN_GP) * stride];
   k.tauT = cache[(long long)(8 * LIN_GP + 1) * stride];
-  k.s = s;
+  k.alpha = cache[(long long)(8 * LIN_GP + 2) * stride];
+  k.K = cache[(long long)(8 * LIN_GP + 3) * stride];
+  k.s = c.h * s;
   scale_coef(k, c);
   return k;
 }
@@ -476,21 +493,21 @@ NC_HD void point_diag(const QP<R>& q, const ElemCoef<R>& k, const ElemConst<R>& 
                       R tcoup[3][8]) {
   R conv[3], rM[3], rT;
   strong(q, k, c, conv, rM, rT);
-  const R w = c.wq, ih = c.inv_h;
+  const R w = c.wh;  // the weight w/h: every term below is h times its physical value
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
     const int ia = a & 1, ja = (a >> 1) & 1, ka = (a >> 2) & 1;
     const R N = R(gfac(ia, gx) * gfac(ja, gy) * gfac(ka, gz));
-    const R D[3] = {R(gsgn(ia) * gfac(ja, gy) * gfac(ka, gz)) * ih,
-                    R(gfac(ia, gx) * gsgn(ja) * gfac(ka, gz)) * ih,
-                    R(gfac(ia, gx) * gfac(ja, gy) * gsgn(ka)) * ih};
+    const R D[3] = {R(gsgn(ia) * gfac(ja, gy) * gfac(ka, gz)),
+                    R(gfac(ia, gx) * gsgn(ja) * gfac(ka, gz)),
+                    R(gfac(ia, gx) * gfac(ja, gy) * gsgn(ka))};
     const R uD = q.u[0] * D[0] + q.u[1] * D[1] + q.u[2] * D[2];
     const R DD = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const R gi = q.G[i][i] + k.alpha;
       out[i][a] += w * (N * N * gi + N * uD + N * k.tau * (D[i] * rM[i] + uD * gi) +
-                        c.Pr * (DD + D[i] * D[i]) + k.tau * uD * uD);
+                        c.prh * (DD + D[i] * D[i]) + k.tau * uD * uD);
       tcoup[i][a] += w * uD * rM[i];
     }
     out[3][a] += w * k.tau * DD;
@@ -502,7 +519,7 @@ template <typename R, int qy, int qz>
 NC_HD void pair_diag(const R xe[5][8], const ElemCoef<R>& k, const ElemConst<R>& c, R out[5][8],
                      R tcoup[3][8]) {
   QP<R> q[2];
-  interp_all_pair<R>(xe, c.inv_h, R(gw(qy)), R(gw(qz)), q);
+  interp_all_pair<R>(xe, R(gw(qy)), R(gw(qz)), q);
   point_diag<R, 0, qy, qz>(q[0], k, c, out, tcoup);
   point_diag<R, 1, qy, qz>(q[1], k, c, out, tcoup);
 }
@@ -521,8 +538,9 @@ NC_HD void elem_diag(const R xe[5][8], R gam, R s, const ElemConst<R>& c, R out[
   pair_diag<R, 1, 0>(xe, k, c, out, tc);
   pair_diag<R, 0, 1>(xe, k, c, out, tc);
   pair_diag<R, 1, 1>(xe, k, c, out, tc);
-  // d tau / d u_{a,i} = -tau^3/(16h^2) u_{a,i}
-  const R dt = -k.tau * k.tau * k.tau * c.inv16h2;
+  // d tau_e / d u_{a,i} = -tau_e^3/(16h^2) u_{a,i}; in the scaled units of tc
+  // (h^2 times physical, the weight w/h) and of tau this is -tau^3/16
+  const R dt = -k.tau * k.tau * k.tau * R(0.0625);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -543,7 +561,7 @@ NC_HD constexpr int pt(int qx, int qy, int qz) { return qx + 2 * qy + 4 * qz; }
 
 // Values and (1/h-scaled) gradients of one Q1 field at the 8 Gauss points.
 template <typename R>
-NC_HD void interp8(const R x[8], R inv_h, R val[8], R g[8][3]) {
+NC_HD void interp8(const R x[8], R val[8], R g[8][3]) {
   const R c[2] = {R(GW0), R(GW1)};
   R dz[4], vz[2][4];
 #pragma unroll
@@ -573,7 +591,7 @@ NC_HD void interp8(const R x[8], R inv_h, R val[8], R g[8][3]) {
 #pragma unroll
     for (int qy = 0; qy < 2; ++qy) {
       const R dx = vyz[qz][qy][1] - vyz[qz][qy][0];
-      const R gxv = dx * inv_h;
+      const R gxv = dx;
 #pragma unroll
       for (int qx = 0; qx < 2; ++qx) {
         val[pt(qx, qy, qz)] = vyz[qz][qy][0] + c[qx] * dx;
@@ -585,7 +603,7 @@ NC_HD void interp8(const R x[8], R inv_h, R val[8], R g[8][3]) {
     const R ey = dy[qz][1] - dy[qz][0];
 #pragma unroll
     for (int qx = 0; qx < 2; ++qx) {
-      const R gyv = (dy[qz][0] + c[qx] * ey) * inv_h;
+      const R gyv = dy[qz][0] + c[qx] * ey;
       g[pt(qx, 0, qz)][1] = gyv;
       g[pt(qx, 1, qz)][1] = gyv;
     }
@@ -595,7 +613,7 @@ NC_HD void interp8(const R x[8], R inv_h, R val[8], R g[8][3]) {
     const R ex = dzy[qy][1] - dzy[qy][0];
 #pragma unroll
     for (int qx = 0; qx < 2; ++qx) {
-      const R gzv = (dzy[qy][0] + c[qx] * ex) * inv_h;
+      const R gzv = dzy[qy][0] + c[qx] * ex;
       g[pt(qx, qy, 0)][2] = gzv;
       g[pt(qx, qy, 1)][2] = gzv;
     }
@@ -605,7 +623,7 @@ NC_HD void interp8(const R x[8], R inv_h, R val[8], R g[8][3]) {
 // Transpose of interp8 (without the 1/h, which the caller folds into F1):
 // out[a] = sum_p [ w N_a(p) f0[p] + dN_a/dxi_j(p) F1[p][j] ] (written, not added:
 // a sum onto zeros would cost an addition per row), with the Gauss
-// weight w of the value slots applied here: wc = w (1 -+ 1/sqrt 3)/2.  The x stage
+// weight of the (h-scaled) value slots applied here: wc = (w/h) (1 -+ 1/sqrt 3)/2.  The x stage
 // takes the two points of a pair to the two nodes: node 1 gets
 // wc0 f0[p0] + wc1 f0[p1] + F, node 0 gets wc1 f0[p0] + wc0 f0[p1] - F (the 1-D
 // weights of node 0 are those of node 1 mirrored), F the pair's x-gradient fluxes.
@@ -663,11 +681,11 @@ NC_HD void test8(R out[8], const R f0[8], const R F1[8][3], const R wc[2]) {
 }
 
 template <typename R>
-NC_HD void interp_all8(const R xe[5][8], R inv_h, QP<R> q[8]) {
+NC_HD void interp_all8(const R xe[5][8], QP<R> q[8]) {
   R val[8], g[8][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    interp8<R>(xe[i], inv_h, val, g);
+    interp8<R>(xe[i], val, g);
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
       q[p].u[i] = val[p];
@@ -676,7 +694,7 @@ NC_HD void interp_all8(const R xe[5][8], R inv_h, QP<R> q[8]) {
       q[p].G[i][2] = g[p][2];
     }
   }
-  interp8<R>(xe[3], inv_h, val, g);
+  interp8<R>(xe[3], val, g);
 #pragma unroll
   for (int p = 0; p < 8; ++p) {
     q[p].p = val[p];
@@ -684,7 +702,7 @@ NC_HD void interp_all8(const R xe[5][8], R inv_h, QP<R> q[8]) {
     q[p].gp[1] = g[p][1];
     q[p].gp[2] = g[p][2];
   }
-  interp8<R>(xe[4], inv_h, val, g);
+  interp8<R>(xe[4], val, g);
 #pragma unroll
   for (int p = 0; p < 8; ++p) {
     q[p].T = val[p];
@@ -715,7 +733,7 @@ NC_HD void elem_residual(const R xe[5][8], R gam, R s, const ElemConst<R>& c, R 
   R S;
   const ElemCoef<R> k = elem_coef(xe, gam, s, c, S);
   QP<R> q[8];
-  interp_all8<R>(xe, c.inv_h, q);
+  interp_all8<R>(xe, q);
   R f0[8][5], F1[8][5][3];
 #pragma unroll
   for (int p = 0; p < 8; ++p) flux_residual(q[p], k, c, f0[p], F1[p]);
@@ -732,11 +750,12 @@ NC_HD void elem_jvp(const R xe[5][8], const R ve[5][8], R gam, R s, const ElemCo
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int a = 0; a < 8; ++a) uv += xe[i][a] * ve[i][a];
-  const R dtau = -k.tau * k.tau * k.tau * c.inv16h2 * uv;
-  const R dtauT = -k.tauT * k.tauT * k.tauT * c.inv16h2 * uv;
+  // d tau_e = -tau_e^3 uv/(16 h^2); scaled (d tau_e / h): -tau^3 uv/16
+  const R dtau = -k.tau * k.tau * k.tau * R(0.0625) * uv;
+  const R dtauT = -k.tauT * k.tauT * k.tauT * R(0.0625) * uv;
   QP<R> q[8], d[8];
-  interp_all8<R>(xe, c.inv_h, q);
-  interp_all8<R>(ve, c.inv_h, d);
+  interp_all8<R>(xe, q);
+  interp_all8<R>(ve, d);
   R f0[8][5], F1[8][5][3];
 #pragma unroll
   for (int p = 0; p < 8; ++p)
@@ -750,14 +769,14 @@ NC_HD void elem_jtvp(const R xe[5][8], const R we[5][8], R gam, R s, const ElemC
   R S;
   const ElemCoef<R> k = elem_coef(xe, gam, s, c, S);
   QP<R> q[8], t[8];
-  interp_all8<R>(xe, c.inv_h, q);
-  interp_all8<R>(we, c.inv_h, t);
+  interp_all8<R>(xe, q);
+  interp_all8<R>(we, t);
   R f0[8][5], F1[8][5][3];
   R tb = R(0), tbT = R(0);
 #pragma unroll
   for (int p = 0; p < 8; ++p) flux_adjoint(q[p], t[p], k, c, f0[p], F1[p], tb, tbT);
   test_all8<R>(out, f0, F1, c.wc);
-  const R gsum = -(k.tau * k.tau * k.tau * tb + k.tauT * k.tauT * k.tauT * tbT) * (c.wq * c.inv16h2);
+  const R gsum = -(k.tau * k.tau * k.tau * tb + k.tauT * k.tauT * k.tauT * tbT) * c.wdt;
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -768,12 +787,15 @@ template <typename R>
 NC_HD R elem_sens(const R xe[5][8], const R le[5][8], R gam, R s, const ElemConst<R>& c) {
   R S;
   const ElemCoef<R> k = elem_coef(xe, gam, s, c, S);
-  const R da = dalpha_of(gam, c), dK = dK_of(gam, c);
+  // design derivatives in the scaled units of the coefficients: d(h alpha_e),
+  // d(K_e/h), and of tau, tau_T from (tau)^-2 = S/16 + t2s + alpha^2 and
+  // (tau_T)^-2 = S/16 + 16 K^2
+  const R da = c.h * dalpha_of(gam, c), dK = c.inv_h * dK_of(gam, c);
   const R dtau = -k.tau * k.tau * k.tau * k.alpha * da;
-  const R dtauT = -k.tauT * k.tauT * k.tauT * k.K * c.k2c * dK;
+  const R dtauT = -k.tauT * k.tauT * k.tauT * k.K * R(16) * dK;
   QP<R> q[8], t[8];
-  interp_all8<R>(xe, c.inv_h, q);
-  interp_all8<R>(le, c.inv_h, t);
+  interp_all8<R>(xe, q);
+  interp_all8<R>(le, t);
   R acc = R(0);
 #pragma unroll
   for (int p = 0; p < 8; ++p) acc += point_sens(q[p], t[p], k, da, dK, dtau, dtauT, c);
@@ -786,7 +808,7 @@ NC_HD void elem_linearize(const R xe[5][8], R gam, R s, const ElemConst<R>& c, R
   R S;
   const ElemCoef<R> k = elem_coef(xe, gam, s, c, S);
   QP<R> q[8];
-  interp_all8<R>(xe, c.inv_h, q);
+  interp_all8<R>(xe, q);
 #pragma unroll
   for (int p = 0; p < 8; ++p) {
     R body[3], rM[3], rT;
@@ -806,6 +828,8 @@ NC_HD void elem_linearize(const R xe[5][8], R gam, R s, const ElemConst<R>& c, R
   }
   cache[(long long)(8 * LIN_GP) * stride] = k.tau;
   cache[(long long)(8 * LIN_GP + 1) * stride] = k.tauT;
+  cache[(long long)(8 * LIN_GP + 2) * stride] = k.alpha;
+  cache[(long long)(8 * LIN_GP + 3) * stride] = k.K;
 }
 
 template <typename R>
@@ -817,10 +841,11 @@ NC_HD void elem_jvp_lin(const R* cache, long long stride, const R ue[3][8], cons
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int a = 0; a < 8; ++a) uv += ue[i][a] * ve[i][a];
-  const R dtau = -k.tau * k.tau * k.tau * c.inv16h2 * uv;
-  const R dtauT = -k.tauT * k.tauT * k.tauT * c.inv16h2 * uv;
+  // d tau_e = -tau_e^3 uv/(16 h^2); scaled (d tau_e / h): -tau^3 uv/16
+  const R dtau = -k.tau * k.tau * k.tau * R(0.0625) * uv;
+  const R dtauT = -k.tauT * k.tauT * k.tauT * R(0.0625) * uv;
   QP<R> d[8];
-  interp_all8<R>(ve, c.inv_h, d);
+  interp_all8<R>(ve, d);
   R f0[8][5], F1[8][5][3];
 #pragma unroll
   for (int P = 0; P < 4; ++P) {
@@ -840,7 +865,7 @@ NC_HD void elem_jtvp_lin(const R* cache, long long stride, const R ue[3][8], con
                           R gam, R s, const ElemConst<R>& c, R out[5][8]) {
   const ElemCoef<R> k = lin_coef(cache, stride, gam, s, c);
   QP<R> t[8];
-  interp_all8<R>(we, c.inv_h, t);
+  interp_all8<R>(we, t);
   R f0[8][5], F1[8][5][3];
   R tb = R(0), tbT = R(0);
 #pragma unroll
@@ -854,7 +879,7 @@ NC_HD void elem_jtvp_lin(const R* cache, long long stride, const R ue[3][8], con
                       tb, tbT);
   }
   test_all8<R>(out, f0, F1, c.wc);
-  const R gsum = -(k.tau * k.tau * k.tau * tb + k.tauT * k.tauT * k.tauT * tbT) * (c.wq * c.inv16h2);
+  const R gsum = -(k.tau * k.tau * k.tau * tb + k.tauT * k.tauT * k.tauT * tbT) * c.wdt;
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -950,13 +975,12 @@ NC_HD void elem_column_lin(const R* cache, long long stride, R ub, int b, R gam,
   const ElemCoef<R> k = lin_coef(cache, stride, gam, s, c);
   R whdtau = R(0), whdtauT = R(0);
   if (G < 3) {  // d(u_e^T u_e)/2 along the direction = u_e(G, b)
-    whdtau = c.wh * (-k.tau * k.tau * k.tau * c.inv16h2 * ub);
-    whdtauT = c.wh * (-k.tauT * k.tauT * k.tauT * c.inv16h2 * ub);
+    whdtau = c.wdt * (-k.tau * k.tau * k.tau * ub);
+    whdtauT = c.wdt * (-k.tauT * k.tauT * k.tauT * ub);
   }
   const R W[2] = {R(GW0), R(GW1)};  // weight of node bit 1 at point bit 0 / 1
   const int bx = b & 1, by = (b >> 1) & 1, bz = (b >> 2) & 1;
-  const R sx = bx ? c.inv_h : -c.inv_h, sy = by ? c.inv_h : -c.inv_h,
-          sz = bz ? c.inv_h : -c.inv_h;
+  const R sx = bx ? R(1) : R(-1), sy = by ? R(1) : R(-1), sz = bz ? R(1) : R(-1);
   R f0[8][5], F1[8][5][3];
 #pragma unroll
   for (int P = 0; P < 4; ++P) {
@@ -1000,21 +1024,22 @@ NC_HD ElemConst<R> make_const(double h, double Gr, double Pr, double amax, doubl
   c.inv_h = R(1.0 / h);
   c.wq = R((h / 2) * (h / 2) * (h / 2));
   c.wh = R((h / 2) * (h / 2) * (h / 2) / h);
-  c.wc[0] = R((h / 2) * (h / 2) * (h / 2) * GW0);
-  c.wc[1] = R((h / 2) * (h / 2) * (h / 2) * GW1);
+  c.wc[0] = R((h / 2) * (h / 2) * (h / 2) / h * GW0);
+  c.wc[1] = R((h / 2) * (h / 2) * (h / 2) / h * GW1);
   c.Pr = R(Pr);
   c.beta = R(Gr * Pr * Pr);
   c.eg[0] = R(eg[0]);
   c.eg[1] = R(eg[1]);
   c.eg[2] = R(eg[2]);
-  c.beg[0] = R(Gr * Pr * Pr * eg[0]);
-  c.beg[1] = R(Gr * Pr * Pr * eg[1]);
-  c.beg[2] = R(Gr * Pr * Pr * eg[2]);
-  c.prw = R(Pr * (h / 2) * (h / 2) * (h / 2) / h);
-  c.prw2 = R(2.0 * Pr * (h / 2) * (h / 2) * (h / 2) / h);
-  c.inv16h2 = R(1.0 / (16.0 * h * h));
-  c.t2inv2 = R((4.0 * Pr / (h * h)) * (4.0 * Pr / (h * h)));
-  c.k2c = R((4.0 / (h * h)) * (4.0 / (h * h)));
+  c.beg[0] = R(h * Gr * Pr * Pr * eg[0]);
+  c.beg[1] = R(h * Gr * Pr * Pr * eg[1]);
+  c.beg[2] = R(h * Gr * Pr * Pr * eg[2]);
+  c.prw = R(Pr * (h / 2) * (h / 2) * (h / 2) / (h * h));
+  c.prw2 = R(2.0 * Pr * (h / 2) * (h / 2) * (h / 2) / (h * h));
+  c.h = R(h);
+  c.prh = R(Pr / h);
+  c.wdt = R((h / 2) * (h / 2) * (h / 2) / h / 16.0);
+  c.t2s = R((4.0 * Pr / h) * (4.0 * Pr / h));
   c.amax = R(amax);
   c.qa = R(qa);
   c.qf = R(qf);

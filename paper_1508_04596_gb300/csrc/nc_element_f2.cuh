@@ -101,14 +101,14 @@ NC_HD Coef2 coef2(const ElemCoef<float>& k) {
 
 // Kernel-wide constants broadcast to both lanes (from ElemConst<float>).
 struct Const2 {
-  f2 wq, wh, Pr, prw, prw2, beg[3], c[2], two;
+  f2 wq, wh, Pr, prw, prw2, beg[3], c[2], two;  // Pr: Pr/h (reference gradients)
 };
 
 NC_HD Const2 const2(const ElemConst<float>& c) {
   Const2 b;
   b.wq = bc2(c.wq);
   b.wh = bc2(c.wh);
-  b.Pr = bc2(c.Pr);
+  b.Pr = bc2(c.prh);
   b.prw = bc2(c.prw);
   b.prw2 = bc2(c.prw2);
   for (int i = 0; i < 3; ++i) b.beg[i] = bc2(c.beg[i]);
@@ -119,9 +119,9 @@ NC_HD Const2 const2(const ElemConst<float>& c) {
 }
 
 // ------------------------------------------------------------------ interpolation
-// Values and (1/h-scaled) gradients of one Q1 field at the 8 Gauss points, as
-// point pairs: val[P], g[P][j].
-NC_HD void interp8_f2(const float x[8], float inv_h, const Const2& K, f2 val[4], f2 g[4][3]) {
+// Values and reference gradients (h grad) of one Q1 field at the 8 Gauss points,
+// as point pairs: val[P], g[P][j].
+NC_HD void interp8_f2(const float x[8], const Const2& K, f2 val[4], f2 g[4][3]) {
   const float c[2] = {float(GW0), float(GW1)};
   // node pairs along x: X[ja][ka]
   const f2 X00 = mk2(x[0], x[1]), X10 = mk2(x[2], x[3]);
@@ -154,30 +154,29 @@ NC_HD void interp8_f2(const float x[8], float inv_h, const Const2& K, f2 val[4],
       const f2 v = VYZ[qz][qy];
       const float dx = v.y - v.x;
       val[P] = mk2(v.x + c[0] * dx, v.x + c[1] * dx);
-      const float gx = dx * inv_h;
-      g[P][0] = mk2(gx, gx);
+      g[P][0] = mk2(dx, dx);
     }
 #pragma unroll
   for (int qz = 0; qz < 2; ++qz) {
     const float ey = DY[qz].y - DY[qz].x;
-    const f2 gy = mk2((DY[qz].x + c[0] * ey) * inv_h, (DY[qz].x + c[1] * ey) * inv_h);
+    const f2 gy = mk2(DY[qz].x + c[0] * ey, DY[qz].x + c[1] * ey);
     g[2 * qz][1] = gy;
     g[1 + 2 * qz][1] = gy;
   }
 #pragma unroll
   for (int qy = 0; qy < 2; ++qy) {
     const float ex = DZY[qy].y - DZY[qy].x;
-    const f2 gz = mk2((DZY[qy].x + c[0] * ex) * inv_h, (DZY[qy].x + c[1] * ex) * inv_h);
+    const f2 gz = mk2(DZY[qy].x + c[0] * ex, DZY[qy].x + c[1] * ex);
     g[qy][2] = gz;
     g[qy + 2][2] = gz;
   }
 }
 
-NC_HD void interp_all_f2(const float xe[5][8], float inv_h, const Const2& K, QP2 q[4]) {
+NC_HD void interp_all_f2(const float xe[5][8], const Const2& K, QP2 q[4]) {
   f2 val[4], g[4][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    interp8_f2(xe[i], inv_h, K, val, g);
+    interp8_f2(xe[i], K, val, g);
 #pragma unroll
     for (int P = 0; P < 4; ++P) {
       q[P].u[i] = val[P];
@@ -186,7 +185,7 @@ NC_HD void interp_all_f2(const float xe[5][8], float inv_h, const Const2& K, QP2
       q[P].G[i][2] = g[P][2];
     }
   }
-  interp8_f2(xe[3], inv_h, K, val, g);
+  interp8_f2(xe[3], K, val, g);
 #pragma unroll
   for (int P = 0; P < 4; ++P) {
     q[P].p = val[P];
@@ -194,7 +193,7 @@ NC_HD void interp_all_f2(const float xe[5][8], float inv_h, const Const2& K, QP2
     q[P].gp[1] = g[P][1];
     q[P].gp[2] = g[P][2];
   }
-  interp8_f2(xe[4], inv_h, K, val, g);
+  interp8_f2(xe[4], K, val, g);
 #pragma unroll
   for (int P = 0; P < 4; ++P) {
     q[P].T = val[P];
@@ -205,9 +204,9 @@ NC_HD void interp_all_f2(const float xe[5][8], float inv_h, const Const2& K, QP2
 }
 
 // ------------------------------------------------------------------ test side
-// Transpose of interp8_f2 (without the 1/h, folded into F1): out[a] =
+// Transpose of interp8_f2 (reference gradients, as in test8): out[a] =
 // sum_p [w N_a(p) f0[p] + dN_a/dxi_j(p) F1[p][j]] (test8, with the value slots'
-// Gauss weight applied here, wc = w (1 -+ 1/sqrt 3)/2), with f0, F1 as point
+// Gauss weight applied here, wc = (w/h) (1 -+ 1/sqrt 3)/2), with f0, F1 as point
 // pairs and out as node pairs out[ja + 2 ka] = (out[a], out[a + 1]).
 NC_HD void test8_f2(f2 out[4], const f2 f0[4], const f2 F1[4][3], const float wc[2],
                     const Const2& K) {
@@ -411,14 +410,14 @@ NC_HD void elem_jvp_f2(const float xe[5][8], const float ve[5][8], float gam, fl
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int a = 0; a < 8; ++a) uv += xe[i][a] * ve[i][a];
-  const float dtau = -ks.tau * ks.tau * ks.tau * c.inv16h2 * uv;
-  const float dtauT = -ks.tauT * ks.tauT * ks.tauT * c.inv16h2 * uv;
+  const float dtau = -ks.tau * ks.tau * ks.tau * 0.0625f * uv;  // scaled units (elem_jvp)
+  const float dtauT = -ks.tauT * ks.tauT * ks.tauT * 0.0625f * uv;
   const Const2 K = const2(c);
   const Coef2 k = coef2(ks);
   const f2 whdtau = bc2(c.wh * dtau), whdtauT = bc2(c.wh * dtauT);
   QP2 q[4], d[4];
-  interp_all_f2(xe, c.inv_h, K, q);
-  interp_all_f2(ve, c.inv_h, K, d);
+  interp_all_f2(xe, K, q);
+  interp_all_f2(ve, K, d);
   f2 f0[4][5], F1[4][5][3];
 #pragma unroll
   for (int P = 0; P < 4; ++P) {
@@ -437,8 +436,8 @@ NC_HD void elem_jtvp_f2(const float xe[5][8], const float we[5][8], float gam, f
   const Const2 K = const2(c);
   const Coef2 k = coef2(ks);
   QP2 q[4], t[4];
-  interp_all_f2(xe, c.inv_h, K, q);
-  interp_all_f2(we, c.inv_h, K, t);
+  interp_all_f2(xe, K, q);
+  interp_all_f2(we, K, t);
   f2 f0[4][5], F1[4][5][3];
   f2 tb = mk2(0.0f, 0.0f), tbT = mk2(0.0f, 0.0f);
 #pragma unroll
@@ -449,8 +448,7 @@ NC_HD void elem_jtvp_f2(const float xe[5][8], const float we[5][8], float gam, f
   }
   test_all_f2(out, f0, F1, c.wc, K);
   const float tbs = tb.x + tb.y, tbTs = tbT.x + tbT.y;
-  const float gsum = -(ks.tau * ks.tau * ks.tau * tbs + ks.tauT * ks.tauT * ks.tauT * tbTs) *
-                     (c.wq * c.inv16h2);
+  const float gsum = -(ks.tau * ks.tau * ks.tau * tbs + ks.tauT * ks.tauT * ks.tauT * tbTs) * c.wdt;
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll

@@ -119,7 +119,7 @@ struct nc_ctx {
   nc_params prm;
   nc_bcs bcs;
   std::vector<nc::Level> lv;
-  double* Y = nullptr;        // element output scratch, 40 * E(level 0) doubles
+  double* Y = nullptr;        // element output scratch, scratch_len(E(level 0)) doubles
   double* partial = nullptr;  // reduction partials, (MAX_RESTART+2) * RED_BLOCKS_MAX doubles
   double* dscal = nullptr;    // device scalars for reductions (MAX_RESTART+2)
   double* src64 = nullptr;    // element source (level 0), FP64
@@ -140,7 +140,16 @@ struct nc_ctx {
 
 namespace nc {
 
-// ---- element operators (nc_kernels.cu); Y is scratch of 40*E elements of R
+// Element-row scratch: the 40 rows (f, a) of the element kernels, in blocks of
+// YB consecutive elements: row r = 8 f + a of element e sits at
+// Y[(e / YB) * 40 YB + r YB + e % YB].  A warp's 32 elements write each row as
+// one contiguous 128-byte (FP32) or 256-byte (FP64) segment, and the 40 rows of an
+// element lie at fixed offsets from its first (offsets known at compile time, so
+// no per-row address arithmetic).  Holds 40 * round_up(E, YB) values.
+constexpr int YB = 32;
+inline long long scratch_len(long long E) { return 40 * ((E + YB - 1) / YB * YB); }
+
+// ---- element operators (nc_kernels.cu); Y is scratch of scratch_len(E) elements of R
 template <typename R>
 void op_residual(const LevelDev& d, const ElemConst<R>& c, const R* x, const R* gam, const R* src,
                  R* r, R* Y, cudaStream_t s);

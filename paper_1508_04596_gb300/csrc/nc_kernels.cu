@@ -1,9 +1,10 @@
 // Element operators, assembly by node-owner gather, and grid transfers.
 //
 // Assembly is colouring-free and deterministic: one thread per element writes
-// its 40 element rows to a scratch array Y[(f*8 + a)*E + e]; one thread per node
-// then sums the rows of its (up to) eight elements in the fixed local order
-// a = 0..7.  No atomics, so results are bitwise reproducible.
+// its 40 element rows (f, a) to a scratch array (blocked by YB elements, see
+// nc_internal.cuh); one thread per node then sums the rows of its (up to) eight
+// elements in the fixed local order a = 0..7.  No atomics, so results are
+// bitwise reproducible.
 #include <type_traits>
 
 #include "nc_element_f2.cuh"
@@ -63,12 +64,20 @@ __device__ __forceinline__ void load_vel(const LevelDev& d, const R* __restrict_
   }
 }
 
+// first row of element e in the blocked scratch; row r = 8 f + a is at + r YB
+__device__ __forceinline__ long long yrow0(long long e) {
+  static_assert(YB == 32, "yrow0 takes the block by a shift");
+  return (e >> 5) * (40 * YB) + (e & (YB - 1));  // e >= 0
+}
+
 template <typename R>
 __device__ __forceinline__ void store_elem(long long E, long long e, const R out[5][8], R* Y) {
+  (void)E;
+  R* y = Y + yrow0(e);
 #pragma unroll
   for (int f = 0; f < 5; ++f)
 #pragma unroll
-    for (int a = 0; a < 8; ++a) Y[(f * 8 + a) * E + e] = out[f][a];
+    for (int a = 0; a < 8; ++a) y[(f * 8 + a) * YB] = out[f][a];
 }
 
 template <typename R>
@@ -224,7 +233,7 @@ __global__ void __launch_bounds__(NODE_THREADS) k_assemble_column(LevelDev d, in
                   9 * (((b >> 2) & 1) - ((a >> 2) & 1) + 1);
 #pragma unroll
     for (int f = 0; f < 5; ++f)
-      if (!((fl >> f) & 1)) S[((long long)(o * 5 + f) * 5 + g) * d.Nn + n] += Y[(f * 8 + a) * d.E + e];
+      if (!((fl >> f) & 1)) S[((long long)(o * 5 + f) * 5 + g) * d.Nn + n] += Y[yrow0(e) + (f * 8 + a) * YB];
   }
 }
 
@@ -284,7 +293,7 @@ __global__ void __launch_bounds__(NODE_THREADS) k_gather(LevelDev d, const R* __
     if (ie < 0 || je < 0 || ke < 0 || ie >= d.nx || je >= d.ny || ke >= d.nz) continue;
     const long long e = ie + (long long)d.nx * (je + (long long)d.ny * ke);
 #pragma unroll
-    for (int f = 0; f < 5; ++f) acc[f] += Y[(f * 8 + a) * d.E + e];
+    for (int f = 0; f < 5; ++f) acc[f] += Y[yrow0(e) + (f * 8 + a) * YB];
   }
   const uint8_t fl = d.flag[n];
   if (MODE == G_RES) {

@@ -119,10 +119,11 @@ extern "C" nc_status nc_jvp_static(const nc_params* prm, const nc_bcs* bcs, cons
   d.nx = prm->nx; d.ny = prm->ny; d.nz = prm->nz; d.h = prm->h;
   d.Nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
   d.E = (long long)d.nx * d.ny * d.nz;
-  // scratch: flags (Nn bytes, rounded up to 256), then 40 rows per element
+  // scratch: flags (Nn bytes, rounded up to 256), then the 40 element rows
+  // (scratch_len(E) values)
   const size_t esz = prec == NC_FP64 ? sizeof(double) : sizeof(float);
   const size_t flag_bytes = ((size_t)d.Nn + 255) / 256 * 256;
-  const double need = (double)flag_bytes + 40.0 * (double)d.E * (double)esz;
+  const double need = (double)flag_bytes + (double)scratch_len(d.E) * (double)esz;
   if (need > (double)kScratchBytes) return NC_ERR_SIZE;
   void* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return NC_ERR_CUDA;

@@ -78,3 +78,23 @@ def test_element_rows_match_the_oracle(tmp_path):
             got = out[5 * k + q]
             err = np.abs(got - ref).max() / np.abs(ref).max()
             assert err <= tol, (k, q, err)
+
+
+def test_flop_counts_match_the_benchmark(tmp_path):
+    """The per-element operation counts that the benchmark's ALU roofline divides
+    by the measured time are those of the element routines as they stand: the
+    routines instantiated with a counting number type
+    (tests/host/element_flop_count.cpp) give exactly bench.FLOPS_PER_ELEM."""
+    import importlib.util
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    exe = str(tmp_path / "flops")
+    subprocess.run([cxx, "-std=c++17", "-O1", os.path.join(HERE, "host", "element_flop_count.cpp"),
+                    "-o", exe], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True, check=True)
+    counts = {l.split()[0]: int(l.split()[1]) for l in r.stdout.strip().splitlines()}
+    spec = importlib.util.spec_from_file_location("bench_consts", os.path.join(HERE, "..", "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    assert counts == bench.FLOPS_PER_ELEM
