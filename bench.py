@@ -38,7 +38,7 @@ DEFAULT_WORKLOAD = "tall192x192x384_gr1e6"
 # flop; an FMA = 2), of the element routines in csrc/nc_element.cuh, counted by
 # instantiating them with a counting number type (tests/host/element_flop_count.cpp;
 # tests/test_element_host.py checks that these figures match it).
-FLOPS_PER_ELEM = {"residual": 1794, "jvp": 3076, "jtvp": 3196, "diag": 6981, "sens": 2892,
+FLOPS_PER_ELEM = {"residual": 1794, "jvp": 3076, "jtvp": 3196, "diag": 6085, "sens": 2852,
                   "linearize": 816, "jvp_lin": 2264, "jtvp_lin": 2384}
 # ALU peaks (whole GPU) from unit counts and the maximum SM clock: 152 SMs x 128
 # FP32 lanes x 2 flop x 2.07 GHz, and 152 SMs x 2 FP64 FMA units x 2 flop x 2.07 GHz
@@ -51,9 +51,9 @@ PEAK_SOURCE = ("unit counts x max SM clock: 152 SMs x 128 FP32 lanes (2 FP64 FMA
 # DRAM traffic of one launch of the headline element kernel, from an ncu capture
 # at the benchmark's workload; used only while the kernel sources are the ones
 # the capture was taken with (their SHA-256 is recorded beside the figure).
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_elem_lin_cached_tall192x192x384_traffic.md")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_elem_lin_cached_tall192x192x384_traffic.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1508_04596_gb300", "csrc", f)
-                  for f in ("nc_kernels.cu", "nc_element.cuh")]
+                  for f in ("nc_kernels.cu", "nc_element.cuh", "nc_internal.cuh")]
 
 
 def parse():

@@ -93,14 +93,17 @@ __global__ void __launch_bounds__(ELEM_THREADS) k_elem_res(LevelDev d, ElemConst
   store_elem(d.E, e, out, Y);
 }
 
-// J v: three blocks per SM (at most 168 registers, a few spilled): 12 warps per SM
-// hide more latency than 8 at 255 registers; measured 9.6 % faster in FP32 and
-// unchanged in FP64.  J^T w, whose fluxes keep more values live, takes two blocks
-// per SM and up to 255 registers: 10 % faster in FP32 than three blocks (its
-// spills at 168 registers cost more than the extra warps gain).  FP32 takes the
-// packed-pair element routines (two lanes of FP32 arithmetic per instruction).
+// Two blocks per SM, up to 255 registers: both products then run without
+// spilling.  J^T w, whose fluxes keep more values live, is 10 % faster in FP32
+// than at three blocks (168 registers, spilled); J v, with fewer values live, is
+// 1.5 % faster at 192x192x384 than at three blocks (where it spills 300 bytes a
+// thread), 0.4 % at 128^3, and as fast as 64-thread blocks at five per SM.
+// FP32 takes the packed-pair element routines (two lanes of FP32 arithmetic per
+// instruction).  The nodal loads stay node by node with 64-bit indices: per-field
+// base pointers with 32-bit row offsets cut the FP32 J v's instructions by 12 %
+// but made it 10 % slower (more long-scoreboard stalls).
 template <typename R, bool TRANSPOSE>
-__global__ void __launch_bounds__(ELEM_THREADS, TRANSPOSE ? 2 : 3) k_elem_lin(LevelDev d, ElemConst<R> c,
+__global__ void __launch_bounds__(ELEM_THREADS, 2) k_elem_lin(LevelDev d, ElemConst<R> c,
                                                            const R* __restrict__ x,
                                                            const R* __restrict__ gam,
                                                            const R* __restrict__ src,

@@ -3,8 +3,10 @@ without a GPU: the element tangent against central differences of the element
 residual, its transpose, diagonal, linearisation-store and design-sensitivity
 variants against it (tests/host/element_consistency_check.cpp), and the
 specialised element columns of the assembled Jacobian against the general
-products (tests/host/element_columns_check.cpp), and the packed-pair FP32
-products against the scalar ones (tests/host/element_pairs_check.cpp)."""
+products (tests/host/element_columns_check.cpp), the packed-pair FP32
+products against the scalar ones (tests/host/element_pairs_check.cpp), the
+element rows against the oracle, and the benchmark's per-element flop figures
+against a count of the routines (tests/host/element_flop_count.cpp)."""
 import os
 import shutil
 import subprocess
