@@ -39,7 +39,7 @@ DEFAULT_WORKLOAD = "tall192x192x384_gr1e6"
 # instantiating them with a counting number type (tests/host/element_flop_count.cpp;
 # tests/test_element_host.py checks that these figures match it).
 FLOPS_PER_ELEM = {"residual": 1794, "jvp": 3076, "jtvp": 3196, "diag": 6085, "sens": 2852,
-                  "linearize": 816, "jvp_lin": 2264, "jtvp_lin": 2384}
+                  "linearize": 848, "jvp_lin": 2214, "jtvp_lin": 2382}
 # ALU peaks (whole GPU) from unit counts and the maximum SM clock: 152 SMs x 128
 # FP32 lanes x 2 flop x 2.07 GHz, and 152 SMs x 2 FP64 FMA units x 2 flop x 2.07 GHz
 # (1.259 TFLOP/s, the GB300's nominal FP64 rate of 1.25).  nc_fma_probe measures

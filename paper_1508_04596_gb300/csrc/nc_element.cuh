@@ -57,6 +57,7 @@ struct ElemConst {
   R h;          // element edge
   R prh;        // Pr/h: the viscous cotangent weight on reference gradients
   R wdt;        // wh/16: weight of the tau derivative terms in scaled units
+  R iwh;        // 1/wh: takes the store's SUPG weights wh tau rM back to tau rM
   R t2s;        // (4 Pr/h)^2 = h^2 tau2^-2: (tau/h)^-2 = S/16 + t2s + (h alpha)^2
   R amax, qa, qf, Ck;
 };
@@ -290,12 +291,15 @@ NC_HD void zero_out(R out[5][8]) {
 // with PARAM, the parameter directions (dalpha, dK); dtau, dtauT are the
 // derivatives of tau, tau_T along the same direction.  Returns f0 (the Gauss
 // weight is applied on the test side) and (w/h)-scaled F1.  Without PARAM,
-// dalpha and dK are not read (J v needs none).
-template <typename R, bool PARAM>
+// dalpha and dK are not read (J v needs none).  With STORE (the products from
+// the linearisation store), rM and rT hold the SUPG weights wtau rM, wtauT rT
+// of the store, and dtau, dtauT the ratios dtau/tau, dtauT/tauT: the terms
+// dtau rM then cost one multiplication each, and the weights none.
+template <typename R, bool PARAM, bool STORE = false>
 NC_HD void flux_tangent_rm(const QP<R>& q, const R rM[3], R rT, const QP<R>& d,
                            const ElemCoef<R>& k, R dalpha, R dK, R dtau, R dtauT,
                            const ElemConst<R>& c, R f0[5], R F1[5][3]) {
-  const R whdtau = c.wh * dtau;
+  const R whdtau = STORE ? dtau : c.wh * dtau;
   R a[3], b[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -307,7 +311,7 @@ NC_HD void flux_tangent_rm(const QP<R>& q, const R rM[3], R rT, const QP<R>& d,
     f0[i] = body;
     // d(tau u_j rM_i) = u_j (dtau rM_i + tau drM_i) + d.u_j (tau rM_i), times wh
     a[i] = whdtau * rM[i] + k.wtau * drM;
-    b[i] = k.wtau * rM[i];
+    b[i] = STORE ? rM[i] : k.wtau * rM[i];
     F1[3][i] = a[i];
   }
   momentum_F1<R, true>(d.G, c.wh * d.p, q.u, a, d.u, b, c, F1);
@@ -315,7 +319,8 @@ NC_HD void flux_tangent_rm(const QP<R>& q, const R rM[3], R rT, const QP<R>& d,
                 q.u[1] * d.gT[1] + q.u[2] * d.gT[2];
   f0[3] = d.G[0][0] + d.G[1][1] + d.G[2][2];
   f0[4] = drT;
-  const R aT = (c.wh * dtauT) * rT + k.wtauT * drT, bT = k.wtauT * rT;
+  const R aT = (STORE ? dtauT : c.wh * dtauT) * rT + k.wtauT * drT;
+  const R bT = STORE ? rT : k.wtauT * rT;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     R t = k.wK * d.gT[j] + q.u[j] * aT + d.u[j] * bT;
@@ -340,7 +345,10 @@ NC_HD void flux_tangent(const QP<R>& q, const QP<R>& d, const ElemCoef<R>& k, R 
 // of tau and tau_T accumulated WITHOUT the Gauss weight w (the caller applies it
 // once per element).  The weight is applied to the outputs rather than to the 20
 // seeds, and the symmetric viscous cotangent is formed once per pair (i, j).
-template <typename R>
+// With STORE, rM and rT hold the store's SUPG weights wtau rM, wtauT rT; the
+// cotangents of tau and tau_T then come out multiplied by wh tau and wh tau_T
+// (the caller divides them out once per element).
+template <typename R, bool STORE = false>
 NC_HD void flux_adjoint_rm(const QP<R>& q, const R rM[3], R rT, const QP<R>& t,
                            const ElemCoef<R>& k, const ElemConst<R>& c, R f0[5], R F1[5][3],
                            R& tau_bar, R& tauT_bar) {
@@ -361,11 +369,11 @@ NC_HD void flux_adjoint_rm(const QP<R>& q, const R rM[3], R rT, const QP<R>& t,
   tauT_bar += C4u * rT;
   const R pb = -(C1[0][0] + C1[1][1] + C1[2][2]);
   R Tb = R(0);
-  const R trT = k.tauT * rT;
+  const R trT = (STORE ? c.iwh : k.tauT) * rT;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    ub[j] = k.tau * (C1[0][j] * rM[0] + C1[1][j] * rM[1] + C1[2][j] * rM[2]) + C1[4][j] * trT +
-            rTb * q.gT[j];
+    ub[j] = (STORE ? c.iwh : k.tau) * (C1[0][j] * rM[0] + C1[1][j] * rM[1] + C1[2][j] * rM[2]) +
+            C1[4][j] * trT + rTb * q.gT[j];
     gTb[j] = k.K * C1[4][j] + rTb * q.u[j];
   }
   {
@@ -443,7 +451,9 @@ NC_HD R point_sens(const QP<R>& q, const QP<R>& t, const ElemCoef<R>& k, R dalph
 // and the element's tau, tau_T can be computed once per linearisation and read
 // back by each product instead of being re-interpolated.  Layout: point g' =
 // 2 * pair + qx (pairs in the order (qy, qz) = (0,0), (1,0), (0,1), (1,1)),
-// LIN_GP values per point (u[3], G[3][3], gT[3], rM[3], rT), then tau, tau_T,
+// LIN_GP values per point (u[3], G[3][3], gT[3], and the SUPG weights of the
+// strong residuals, wtau rM[3] and wtauT rT, which the products use as they
+// are), then tau, tau_T,
 // alpha, K (all in the scaled units of the point quantities, see Scaling; alpha
 // and K are stored so that the products need no division);
 // slot s of an element is stored at cache[s * stride].
@@ -823,8 +833,8 @@ NC_HD void elem_linearize(const R xe[5][8], R gam, R s, const ElemConst<R>& c, R
 #pragma unroll
     for (int j = 0; j < 3; ++j) o[(12 + j) * stride] = q[p].gT[j];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) o[(15 + i) * stride] = rM[i];
-    o[18 * stride] = rT;
+    for (int i = 0; i < 3; ++i) o[(15 + i) * stride] = k.wtau * rM[i];
+    o[18 * stride] = k.wtauT * rT;
   }
   cache[(long long)(8 * LIN_GP) * stride] = k.tau;
   cache[(long long)(8 * LIN_GP + 1) * stride] = k.tauT;
@@ -841,9 +851,9 @@ NC_HD void elem_jvp_lin(const R* cache, long long stride, const R ue[3][8], cons
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int a = 0; a < 8; ++a) uv += ue[i][a] * ve[i][a];
-  // d tau_e = -tau_e^3 uv/(16 h^2); scaled (d tau_e / h): -tau^3 uv/16
-  const R dtau = -k.tau * k.tau * k.tau * R(0.0625) * uv;
-  const R dtauT = -k.tauT * k.tauT * k.tauT * R(0.0625) * uv;
+  // the store holds wtau rM: the tangent takes dtau/tau = -tau^2 uv/16 (scaled units)
+  const R rdtau = -k.tau * k.tau * R(0.0625) * uv;
+  const R rdtauT = -k.tauT * k.tauT * R(0.0625) * uv;
   QP<R> d[8];
   interp_all8<R>(ve, d);
   R f0[8][5], F1[8][5][3];
@@ -854,8 +864,8 @@ NC_HD void elem_jvp_lin(const R* cache, long long stride, const R ue[3][8], cons
     load_lin_pair<R>(cache, stride, P, q, rM, rT);
 #pragma unroll
     for (int sx = 0; sx < 2; ++sx)
-      flux_tangent_rm<R, false>(q[sx], rM[sx], rT[sx], d[2 * P + sx], k, R(0), R(0), dtau, dtauT,
-                                c, f0[2 * P + sx], F1[2 * P + sx]);
+      flux_tangent_rm<R, false, true>(q[sx], rM[sx], rT[sx], d[2 * P + sx], k, R(0), R(0), rdtau,
+                                      rdtauT, c, f0[2 * P + sx], F1[2 * P + sx]);
   }
   test_all8<R>(out, f0, F1, c.wc);
 }
@@ -875,11 +885,12 @@ NC_HD void elem_jtvp_lin(const R* cache, long long stride, const R ue[3][8], con
     load_lin_pair<R>(cache, stride, P, q, rM, rT);
 #pragma unroll
     for (int sx = 0; sx < 2; ++sx)
-      flux_adjoint_rm(q[sx], rM[sx], rT[sx], t[2 * P + sx], k, c, f0[2 * P + sx], F1[2 * P + sx],
-                      tb, tbT);
+      flux_adjoint_rm<R, true>(q[sx], rM[sx], rT[sx], t[2 * P + sx], k, c, f0[2 * P + sx],
+                               F1[2 * P + sx], tb, tbT);
   }
   test_all8<R>(out, f0, F1, c.wc);
-  const R gsum = -(k.tau * k.tau * k.tau * tb + k.tauT * k.tauT * k.tauT * tbT) * c.wdt;
+  // tb, tbT carry the store's factors wh tau, wh tauT: tau^3 tb wdt becomes tau^2 tb / 16
+  const R gsum = -(k.tau * k.tau * tb + k.tauT * k.tauT * tbT) * R(0.0625);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -890,8 +901,9 @@ NC_HD void elem_jtvp_lin(const R* cache, long long stride, const R ue[3][8], con
 // Pointwise tangent fluxes for a unit direction on one unknown of one node: phi
 // = N_b and psi = grad N_b at the point, on unknown G (0-2 a velocity component,
 // 3 the pressure, 4 the temperature).  The same terms as flux_tangent_rm with
-// every product by a zero of the direction left out; dtau, dtauT are zero for
-// G >= 3 (tau depends on the velocities only).
+// STORE (rM, rT the store's SUPG weights wtau rM, wtauT rT; whdtau, whdtauT the
+// ratios dtau/tau, dtauT/tauT) with every product by a zero of the direction
+// left out; the ratios are zero for G >= 3 (tau depends on the velocities only).
 template <typename R, int G>
 NC_HD void flux_column(const QP<R>& q, const R rM[3], R rT, R phi, const R psi[3],
                        const ElemCoef<R>& k, R whdtau, R whdtauT, const ElemConst<R>& c, R f0[5],
@@ -905,7 +917,7 @@ NC_HD void flux_column(const QP<R>& q, const R rM[3], R rT, R phi, const R psi[3
       if (i == G) body += upsi + k.alpha * phi;
       f0[i] = body;
       a[i] = whdtau * rM[i] + k.wtau * body;
-      b[i] = k.wtau * rM[i];
+      b[i] = rM[i];
       F1[3][i] = a[i];
     }
 #pragma unroll
@@ -922,7 +934,7 @@ NC_HD void flux_column(const QP<R>& q, const R rM[3], R rT, R phi, const R psi[3
     const R drT = phi * q.gT[G];
     f0[3] = psi[G];
     f0[4] = drT;
-    const R aT = whdtauT * rT + k.wtauT * drT, bT = k.wtauT * rT;
+    const R aT = whdtauT * rT + k.wtauT * drT, bT = rT;
 #pragma unroll
     for (int j = 0; j < 3; ++j) F1[4][j] = j == G ? q.u[j] * aT + phi * bT : q.u[j] * aT;
   } else if (G == 3) {
@@ -975,8 +987,9 @@ NC_HD void elem_column_lin(const R* cache, long long stride, R ub, int b, R gam,
   const ElemCoef<R> k = lin_coef(cache, stride, gam, s, c);
   R whdtau = R(0), whdtauT = R(0);
   if (G < 3) {  // d(u_e^T u_e)/2 along the direction = u_e(G, b)
-    whdtau = c.wdt * (-k.tau * k.tau * k.tau * ub);
-    whdtauT = c.wdt * (-k.tauT * k.tauT * k.tauT * ub);
+    // the store holds wtau rM: the ratio dtau/tau = -tau^2 ub/16 (scaled units)
+    whdtau = -k.tau * k.tau * R(0.0625) * ub;
+    whdtauT = -k.tauT * k.tauT * R(0.0625) * ub;
   }
   const R W[2] = {R(GW0), R(GW1)};  // weight of node bit 1 at point bit 0 / 1
   const int bx = b & 1, by = (b >> 1) & 1, bz = (b >> 2) & 1;
@@ -1039,6 +1052,7 @@ NC_HD ElemConst<R> make_const(double h, double Gr, double Pr, double amax, doubl
   c.h = R(h);
   c.prh = R(Pr / h);
   c.wdt = R((h / 2) * (h / 2) * (h / 2) / h / 16.0);
+  c.iwh = R(h / ((h / 2) * (h / 2) * (h / 2)));
   c.t2s = R((4.0 * Pr / h) * (4.0 * Pr / h));
   c.amax = R(amax);
   c.qa = R(qa);
