@@ -50,9 +50,7 @@ struct ElemConst {
   R wh;         // wq / h: weight of the gradient-slot fluxes F1
   R wc[2];      // (wq/h) (1 -+ 1/sqrt 3)/2: the Gauss weight times the 1-D shape-function
                 // weights of the (h-scaled) value-slot fluxes f0 (applied on the test side)
-  R Pr, beta;   // Pr, Gr Pr^2
-  R eg[3];      // unit gravity direction
-  R beg[3];     // h beta eg (buoyancy in the h-scaled strong residual)
+  R beg[3];     // h Gr Pr^2 e^g (buoyancy in the h-scaled strong residual)
   R prw, prw2;  // Pr wh/h, 2 Pr wh/h (viscous fluxes of reference gradients)
   R h;          // element edge
   R prh;        // Pr/h: the viscous cotangent weight on reference gradients
@@ -484,6 +482,7 @@ NC_HD void load_lin_pair(const R* cache, long long stride, int P, QP<R> q[2], R 
 
 template <typename R>
 NC_HD ElemCoef<R> lin_coef(const R* cache, long long stride, R gam, R s, const ElemConst<R>& c) {
+  (void)gam;  // alpha and K come from the store
   ElemCoef<R> k;
   k.tau = cache[(long long)(8 * LIN_GP) * stride];
   k.tauT = cache[(long long)(8 * LIN_GP + 1) * stride];
@@ -1039,11 +1038,6 @@ NC_HD ElemConst<R> make_const(double h, double Gr, double Pr, double amax, doubl
   c.wh = R((h / 2) * (h / 2) * (h / 2) / h);
   c.wc[0] = R((h / 2) * (h / 2) * (h / 2) / h * GW0);
   c.wc[1] = R((h / 2) * (h / 2) * (h / 2) / h * GW1);
-  c.Pr = R(Pr);
-  c.beta = R(Gr * Pr * Pr);
-  c.eg[0] = R(eg[0]);
-  c.eg[1] = R(eg[1]);
-  c.eg[2] = R(eg[2]);
   c.beg[0] = R(h * Gr * Pr * Pr * eg[0]);
   c.beg[1] = R(h * Gr * Pr * Pr * eg[1]);
   c.beg[2] = R(h * Gr * Pr * Pr * eg[2]);
