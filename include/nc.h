@@ -422,7 +422,12 @@ nc_status nc_prolong_state(nc_ctx* ctx, int level, const double* x_coarse, doubl
  * most).  lambda_inout receives the solution; on entry it holds the initial
  * guess when opts->adjoint_start = 1 and is not read otherwise (start from 0).
  * info->res0 is ||rhs||, the refinement residuals go to info->res_hist (the
- * first one that of the initial guess).  All FP64 [5][Nn].  Synchronous. */
+ * first one that of the initial guess).  The FP64 products J^T lambda of the
+ * refinement come from an FP64 linearisation store of the finest grid: the FP64
+ * solver's own (mixed = 0), or, with mixed = 1, one the context allocates at the
+ * first adjoint solve (156 doubles per element, released by nc_destroy) when the
+ * device keeps at least 8 GB free after it; otherwise they re-interpolate the
+ * state.  All FP64 [5][Nn].  Synchronous. */
 nc_status nc_adjoint_solve(nc_ctx* ctx, const double* x, const double* gamma,
                            const double* rhs, double* lambda_inout, const nc_solve_opts* opts,
                            nc_solve_info* info, void* stream);

@@ -201,6 +201,7 @@ void nc_destroy(nc_ctx* ctx) {
   cudaFree(ctx->cjel);
   for (auto& p : ctx->filt) cudaFree(p);
   cudaFree(ctx->pub_lin);
+  cudaFree(ctx->ref_lin);
   cudaFree(ctx->asm_lin);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
   delete ctx;

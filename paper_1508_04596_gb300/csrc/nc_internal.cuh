@@ -133,6 +133,7 @@ struct nc_ctx {
   double* filt[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // filter CG
   double* pub_lin = nullptr;  // linearisation of nc_linearize (level 0, FP64)
   double* asm_lin = nullptr;  // linearisation used by nc_assemble (level 0, FP64)
+  double* ref_lin = nullptr;  // linearisation of the mixed adjoint's FP64 refinement (level 0)
   const double* pub_x = nullptr;
   const double* pub_gam = nullptr;
   std::string err;

@@ -856,6 +856,32 @@ nc_status nc_mg_apply(nc_ctx* ctx, int level, const double* x, const double* gam
   return st != NC_OK ? st : st2;
 }
 
+}  // extern "C"
+
+namespace {
+// FP64 linearisation store of the finest level for the mixed adjoint's
+// refinement residuals (156 doubles per element), allocated on first use when
+// the device keeps at least 8 GB free after it; false if it does not fit.
+bool refine_store(nc_ctx* ctx, long long E) {
+  if (ctx->ref_lin) return true;
+  const size_t need = sizeof(double) * (size_t)LIN_SLOTS * (size_t)E;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (fr < need + ((size_t)8 << 30)) return false;
+  if (cudaMalloc((void**)&ctx->ref_lin, need) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->ref_lin = nullptr;
+    return false;
+  }
+  return true;
+}
+}  // namespace
+
+extern "C" {
+
 nc_status nc_adjoint_solve(nc_ctx* ctx, const double* x, const double* gam, const double* rhs,
                            double* lam, const nc_solve_opts* opts, nc_solve_info* info_out,
                            void* stream) {
@@ -880,28 +906,41 @@ nc_status nc_adjoint_solve(nc_ctx* ctx, const double* x, const double* gam, cons
     st = norm2(ctx, n, rhs, &nb, s);
     info.res0 = nb;
     double nr = nb;
-    if (o.adjoint_start) {  // warm start: the FP64 residual of the given lambda
-      op_jtvp<double>(L.d, L.c64, x, gam, ctx->src64, lam, t, ctx->Y, s);
+    // the state and the design do not change during the refinement: one
+    // linearisation of every level serves all sweeps
+    if (st == NC_OK)
+      st = mixed ? linearize<float>(ctx, nlev, x, gam, s, o) : linearize<double>(ctx, nlev, x, gam, s, o);
+    // FP64 refinement residuals r = rhs - J^T lam from an FP64 linearisation store
+    // of the finest level: the FP64 solver's own, or in mixed mode one made here
+    // when the device has room for it (else the state is re-interpolated)
+    const double* store = nullptr;
+    if (st == NC_OK) {
+      if (!mixed) {
+        store = L.f64.lin;
+      } else if (refine_store(ctx, L.d.E)) {
+        op_linearize<double>(L.d, L.c64, x, gam, ctx->src64, ctx->ref_lin, s);
+        store = ctx->ref_lin;
+      }
+    }
+    auto jt64 = [&](const double* w, double* out) {
+      if (store)
+        op_jtvp_cached<double>(L.d, L.c64, x, gam, ctx->src64, store, w, out, ctx->Y, s);
+      else
+        op_jtvp<double>(L.d, L.c64, x, gam, ctx->src64, w, out, ctx->Y, s);
+    };
+    if (st == NC_OK && o.adjoint_start) {  // warm start: the FP64 residual of the given lambda
+      jt64(lam, t);
       vwaxpy(n, rhs, -1.0, (const double*)t, r, s);
-      if (st == NC_OK) st = norm2(ctx, n, r, &nr, s);
-    } else {
+      st = norm2(ctx, n, r, &nr, s);
+    } else if (st == NC_OK) {
       vzero(n, lam, s);
       vcopy(n, rhs, r, s);
     }
     info.res_hist[0] = nr;
     const LinSolve ls{true, mixed, nlev};
     int k = 0;
-    // the state and the design do not change during the refinement: one
-    // linearisation of every level serves all sweeps
-    bool linearized = false;
     while (st == NC_OK && nr > o.rtol_adjoint * nb && nr > 0.0) {
       if (k >= o.max_newton) { st = set_err(ctx, NC_ERR_MAXIT, "adjoint refinement limit"); break; }
-      if (!linearized) {
-        st = mixed ? linearize<float>(ctx, nlev, x, gam, s, o)
-                   : linearize<double>(ctx, nlev, x, gam, s, o);
-        if (st != NC_OK) break;
-        linearized = true;
-      }
       int lits = 0;
       // inner relative tolerance: no tighter than needed for the outer target
       const double rt = std::fmax(o.rtol_lin, 0.5 * o.rtol_adjoint * nb / nr);
@@ -910,7 +949,7 @@ nc_status nc_adjoint_solve(nc_ctx* ctx, const double* x, const double* gam, cons
       if (st != NC_OK && st != NC_ERR_MAXIT) break;
       vaxpy(n, 1.0, (const double*)dl, lam, s);
       // FP64 refinement residual r = rhs - J^T lam
-      op_jtvp<double>(L.d, L.c64, x, gam, ctx->src64, lam, t, ctx->Y, s);
+      jt64(lam, t);
       vwaxpy(n, rhs, -1.0, (const double*)t, r, s);
       if ((st = norm2(ctx, n, r, &nr, s)) != NC_OK) break;
       ++k;
