@@ -38,7 +38,7 @@ DEFAULT_WORKLOAD = "tall192x192x384_gr1e6"
 # flop; an FMA = 2), of the element routines in csrc/nc_element.cuh, counted by
 # instantiating them with a counting number type (tests/host/element_flop_count.cpp;
 # tests/test_element_host.py checks that these figures match it).
-FLOPS_PER_ELEM = {"residual": 1794, "jvp": 3076, "jtvp": 3196, "diag": 6085, "sens": 2852,
+FLOPS_PER_ELEM = {"residual": 1794, "jvp": 3076, "jtvp": 3196, "diag": 6085, "sens": 1796,
                   "linearize": 848, "jvp_lin": 2214, "jtvp_lin": 2382}
 # ALU peaks (whole GPU) from unit counts and the maximum SM clock: 152 SMs x 128
 # FP32 lanes x 2 flop x 2.07 GHz, and 152 SMs x 2 FP64 FMA units x 2 flop x 2.07 GHz

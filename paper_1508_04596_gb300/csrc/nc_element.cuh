@@ -419,27 +419,34 @@ NC_HD void flux_adjoint(const QP<R>& q, const QP<R>& t, const ElemCoef<R>& k,
 }
 
 // ---------------------------------------------------------------------------- design derivative
+// lambda^T dr/dgamma at one Gauss point: the tangent fluxes of flux_tangent_rm
+// in the parameter directions alone (the state direction is zero), contracted
+// with the test field t.  With no state direction only these terms remain:
+//   f0_M[i] = dalpha u_i,   F1_M[i][j] = u_j a_i,   F1_C[i] = a_i,
+//   a_i = wh (dtau rM_i + tau dalpha u_i),
+//   F1_T[j] = u_j wh dtauT rT + wh dK grad_j T,
+// so the contraction is  wh sum_i f0_M[i] t.u_i
+//   + sum_i a_i (u . grad t_i + d_i t_p) + wh dtauT rT (u . grad t_T)
+//   + wh dK (grad T . grad t_T)
+// (f0 is h-scaled and takes the weight w/h; F1 carries w/h and meets the test
+// gradients in reference units, which supply the missing h).
 template <typename R>
 NC_HD R point_sens(const QP<R>& q, const QP<R>& t, const ElemCoef<R>& k, R dalpha, R dK, R dtau,
                    R dtauT, const ElemConst<R>& c) {
-  QP<R> zero;
-  zero.p = zero.T = R(0);
+  R body[3], rM[3], rT;
+  strong(q, k, c, body, rM, rT);
+  const R whdtau = c.wh * dtau;
+  R acc = R(0), acc1 = R(0);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    zero.u[i] = zero.gp[i] = zero.gT[i] = R(0);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) zero.G[i][j] = R(0);
+    const R f0 = dalpha * q.u[i];
+    acc += f0 * t.u[i];
+    const R a = whdtau * rM[i] + k.wtau * f0;
+    acc1 += a * (q.u[0] * t.G[i][0] + q.u[1] * t.G[i][1] + q.u[2] * t.G[i][2] + t.gp[i]);
   }
-  R f0[5], F1[5][3];
-  flux_tangent<R, true>(q, zero, k, dalpha, dK, dtau, dtauT, c, f0, F1);
-  // f0 (h-scaled) carries no weight: multiply by w/h once; F1 carries w/h and
-  // meets the test gradient t in reference units, which supplies the missing h
-  R acc = f0[0] * t.u[0] + f0[1] * t.u[1] + f0[2] * t.u[2] + f0[3] * t.p + f0[4] * t.T;
-  R acc1 = R(0);
-#pragma unroll
-  for (int j = 0; j < 3; ++j)
-    acc1 += F1[0][j] * t.G[0][j] + F1[1][j] * t.G[1][j] + F1[2][j] * t.G[2][j] +
-            F1[3][j] * t.gp[j] + F1[4][j] * t.gT[j];
+  const R ugT = q.u[0] * t.gT[0] + q.u[1] * t.gT[1] + q.u[2] * t.gT[2];
+  const R gTgT = q.gT[0] * t.gT[0] + q.gT[1] * t.gT[1] + q.gT[2] * t.gT[2];
+  acc1 += (c.wh * dtauT) * rT * ugT + (c.wh * dK) * gTgT;
   return c.wh * acc + acc1;
 }
 
