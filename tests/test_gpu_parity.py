@@ -386,6 +386,40 @@ def test_largest_config_sampled_rows(nc):
     assert err <= TOL64, ("jtvp_lin", err)
 
 
+def test_largest_config_mixed_solve_matches_fp64(nc):
+    """192 x 192 x 384 (71.7M unknowns, Gr = 1e6, flux-heated patch): the
+    mixed-precision state, adjoint and sensitivity solve of one design iteration
+    agrees with the plain FP64 solve on the same GPU to 1e-8 (state and the
+    sensitivities of all 14.16M elements), as the benchmark's design iteration
+    runs it: a cold mixed state solve of the design by grid sequencing, one
+    synthetic design step, then per precision the warm Newton solve to 1e-8, the
+    objective's gradient, the adjoint to 1e-10 and the sensitivities.  The oracle's
+    direct solves do not reach this size; their agreement with both modes is
+    tested at 12^3 and 8^3."""
+    name = "tall192x192x384_gr1e6"
+    prob = nc.Problem.from_workload(name, patch="flux")
+    g0h = synth.design(name)
+    g0 = dev(g0h)
+    g1 = dev(synth.design_step(name, g0h, 77))
+    x0 = torch.zeros(prob.ndof, dtype=torch.float64, device="cuda")
+    prob.newton_solve_sequenced(g0, x0, nc.default_opts(mixed=1, ramp_steps=3))
+    out = {}
+    for mixed in (1, 0):
+        x = x0.clone()
+        _, info = prob.newton_solve(g1, x, nc.default_opts(mixed=mixed, rtol_newton=1e-8,
+                                                           ramp_steps=3))
+        assert info["status"] == "NC_OK", (mixed, info["status"])
+        _, dphi = prob.objective(x)
+        lam, ainfo = prob.adjoint_solve(x, g1, -dphi, opts=nc.default_opts(mixed=mixed))
+        assert ainfo["status"] == "NC_OK", (mixed, ainfo["status"])
+        out[mixed] = (x, prob.sensitivity(x, g1, lam))
+        del lam, dphi
+    (xm, sm), (xd, sd) = out[1], out[0]
+    err_x = float(torch.linalg.norm(xm - xd) / torch.linalg.norm(xd))
+    err_s = float(torch.linalg.norm(sm - sd) / torch.linalg.norm(sd))
+    assert err_x <= 1e-8 and err_s <= 1e-8, (err_x, err_s)
+
+
 def test_newton_matches_oracle_cfg0(nc):
     """cavity12_gr1e3: Newton-FGMRES-multigrid (FP64 and mixed) converges to the
     oracle's direct-solve Newton solution."""
